@@ -1,0 +1,180 @@
+/*
+ * hopf.h - C ABI of the GB300 generalized-Hopf primal-dual solver.
+ *
+ * The library evaluates, for very many independent query points at once,
+ * the generalized Hopf formula for the linear system  xdot = A x + B u
+ * (Kirchner, Hewer, Darbon, Osher, "A Primal-Dual Method for Optimal Control
+ * and Trajectory Generation in High-Dimensional Systems"):
+ *
+ *   phi(x, T) = -min_p { J_z*(p) + sum_i w_i |K_i p|_* - <x, p> }      (Eq. 18)
+ *   K_i = (-e^{-(T - t_i) A} B Q)^T                                      (Eq. 20)
+ *
+ * with a ball or box control set (support function = dual norm, §III.A,
+ * Eq. 16) and the ellipsoidal target  { x : x^T W^-1 x <= 1 }  whose terminal
+ * cost is J_x(x) = x^T W^-1 x - 1 (§VI.A, Eq. 34 - Eq. 35).  The minimisation
+ * is the Chambolle-Pock iteration of Eq. 15 with the separable prox of
+ * Eq. 23 and the quadratic prox of Eq. 37.  On top of it sit the minimum
+ * time to reach the target (§IV) and the optimal control and trajectory
+ * generated from the optimal dual p* (Eq. 27, Eq. 33).
+ *
+ * Conventions shared by every entry point
+ *  - Problem matrices (A, B, W, half_widths) are HOST float64 arrays, row
+ *    major, read during the call only; the caller keeps ownership.
+ *  - Per-point arrays (x, t, outputs) are caller-owned DEVICE arrays unless
+ *    opts->host_io is non-zero, in which case they are HOST arrays and the
+ *    library copies them to and from the device inside the call (the call
+ *    then returns after the results are back on the host).
+ *  - Element type of per-point float arrays: double when opts->precision is
+ *    HOPF_FP64, float otherwise.  Integer outputs are int32.
+ *  - Calls are ordered on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream).  hopf_value and hopf_trajectory do not synchronise the host
+ *    unless host_io is set; hopf_time_to_reach reads one int32 per
+ *    bisection step back to the host to know when every point has finished.
+ *  - The library keeps a grow-only device workspace per device (released by
+ *    hopf_release_workspace).  Concurrent calls from several host threads are
+ *    serialised by an internal lock.
+ *  - Return value: HOPF_SUCCESS (0) or a negative HOPF_E* code; the message
+ *    of the last failure is available from hopf_last_error().  Per-point
+ *    outcomes are reported separately in status[] (HOPF_OK, ...).
+ */
+#ifndef HOPF_GB300_H
+#define HOPF_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* control set kinds (§III.A) */
+#define HOPF_BALL 0 /* {u : |u|_2 <= radius}; dual norm = 2-norm            */
+#define HOPF_BOX 1  /* {u : |u_j| <= half_widths[j]}; dual norm = 1-norm     */
+
+/* quadrature rules (§III.A, Eq. 17 and the trapezoid rule it mentions) */
+#define HOPF_LEFT_RIEMANN 0 /* t_i = i T/N, i = 0..N-1, weights T/N          */
+#define HOPF_TRAPEZOID 1    /* t_i = i T/(N-1), end weights halved           */
+
+/* arithmetic of the iteration */
+#define HOPF_FP64 0 /* float64 everywhere                                    */
+#define HOPF_FP32 1 /* float64 tables, float32 iteration and certificates    */
+
+/* per-point status */
+#define HOPF_OK 0             /* certified: relative duality gap <= tol_gap      */
+#define HOPF_MAXITER 1        /* max_iter reached; outputs are the last iterate  */
+#define HOPF_NONFINITE 2      /* NaN/Inf met in the iteration                    */
+#define HOPF_UNREACHABLE 3    /* time-to-reach: phi(x, t_max) > 0                */
+#define HOPF_AMBIGUOUS_SIGN 4 /* time-to-reach: |phi| below the certificate    */
+
+/* return codes */
+#define HOPF_SUCCESS 0
+#define HOPF_EINVAL (-1)       /* bad size, pointer or option                   */
+#define HOPF_ENOTSPD (-2)      /* W is not symmetric positive definite          */
+#define HOPF_ECUDA (-3)        /* a CUDA runtime call failed                    */
+#define HOPF_ENOMEM (-4)       /* device allocation failed                      */
+#define HOPF_ENONFINITE (-5)   /* non-finite A, B, W or bounds                  */
+
+typedef struct {
+    int n;                      /* state dimension, >= 1                         */
+    int m;                      /* control dimension, >= 1                       */
+    const double *A;            /* host, n*n row-major: xdot = A x + B u (Eq. 8) */
+    const double *B;            /* host, n*m row-major                            */
+    int ctrl_kind;              /* HOPF_BALL or HOPF_BOX                          */
+    double radius;              /* ball radius (HOPF_BALL), > 0                   */
+    const double *half_widths;  /* host, m, > 0 (HOPF_BOX; ignored for a ball)    */
+    const double *W;            /* host, n*n SPD: target {x : x^T W^-1 x <= 1}    */
+} hopf_problem;
+
+typedef struct {
+    int rule;           /* HOPF_LEFT_RIEMANN or HOPF_TRAPEZOID                    */
+    int N;              /* quadrature nodes (>= 1; >= 2 for the trapezoid rule)   */
+    int max_iter;       /* iteration cap per solve                                */
+    int gap_every;      /* duality-gap check period g (>= 1)                      */
+    int precision;      /* HOPF_FP64 or HOPF_FP32                                 */
+    int host_io;        /* 0: per-point arrays are device pointers; 1: host       */
+    double tau;         /* primal step (> 0)                                      */
+    double sigma_scale; /* dual step sigma = sigma_scale / (tau |K|^2), (0, 1]    */
+    double tol_gap;     /* stop when (P - D) / max(1, |P|, |D|) <= tol_gap        */
+    double t_max;       /* time-to-reach: bisection bracket [0, t_max]            */
+    double tol_T;       /* time-to-reach: stop when hi - lo <= tol_T * hi         */
+    int profile;        /* non-zero: record CUDA events around the table build
+                           and the solve kernel of hopf_value (see
+                           hopf_last_profile)                                     */
+} hopf_opts;
+
+/* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,
+ * gap_every 8, FP32, device io, tau 1, sigma_scale 1 (§VI: sigma = 1/(tau |K|^2)),
+ * tol_gap 1e-5, t_max 10, tol_T 1e-5. */
+void hopf_default_opts(hopf_opts *opts);
+
+/*
+ * hopf_value - phi(x_k, t_k) of Eq. 18 for P query points (§III.A, §VI).
+ *   x       [P*n]  query states (at time zero, so z0 = x, Eq. 9)
+ *   t       [1] if t_stride == 0 (one horizon for every point: one shared
+ *           node table), else [P] per-point horizons (t_stride == 1; one table
+ *           per point).  t >= 0; t = 0 gives phi = J_x(x).
+ *   p_init  NULL (cold start of §VI: p0 = x, y0 = K x) or [P*n] warm start
+ *           (p0 = p_init, y0_i = w_i argmax_{c in U} <c, K_i p0>).
+ *   phi     [P]    -P(pbar): certified to lie within gap of the exact value
+ *   p_star  [P*n]  the primal point of the certificate (approximates p*, Eq. 24)
+ *   gap     [P]    relative duality gap of the certificate
+ *   iters   [P]    iterations used
+ *   status  [P]    HOPF_OK / HOPF_MAXITER / HOPF_NONFINITE
+ * P = 0 is allowed and does nothing.
+ */
+int hopf_value(const hopf_problem *prob, const hopf_opts *opts, int P,
+               const void *x, const void *t, int t_stride, const void *p_init,
+               void *phi, void *p_star, void *gap, int *iters, int *status,
+               void *stream);
+
+/*
+ * hopf_time_to_reach - minimum time T* with phi(x, T*) <= 0 (§IV), by
+ * bisection on [lo_k, hi_k] (default [0, opts->t_max]).  The sign of phi at a
+ * candidate horizon is read from the certified interval phi in [-P, -D]; the
+ * iteration at that horizon stops as soon as the interval excludes zero.
+ *   x        [P*n]
+ *   T_lo,T_hi NULL, or [P] per-point bracket (warm start: a bracket known to
+ *            contain T*; a wrong bracket is detected by the two end-point signs
+ *            and replaced by [0, t_max])
+ *   p_init   NULL or [P*n]: warm start of every inner solve
+ *   T_star   [P]  hi at termination (0 inside the target; t_max if unreachable)
+ *   p_star   [P*n] certificate primal point at T_star (solved to tol_gap)
+ *   gap      [P]  relative gap of that final solve
+ *   status   [P]  HOPF_OK / HOPF_UNREACHABLE / HOPF_MAXITER / HOPF_AMBIGUOUS_SIGN
+ *   steps    NULL or host int*: number of bisection steps taken
+ */
+int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P,
+                       const void *x, const void *T_lo, const void *T_hi,
+                       const void *p_init, void *T_star, void *p_star, void *gap,
+                       int *status, int *steps, void *stream);
+
+/*
+ * hopf_trajectory - optimal control and state on S uniform steps of [0, T_k]
+ * generated from p*_k (§IV Eq. 27, §V Eq. 33).  With h = T/S and s_j = j h:
+ *   u_j = Q argmax_{c in U} <c, -Q^T B^T e^{-s_j A^T} p*>,
+ *   x_j = e^{h A} x_{j-1} + h B u_j,  x_0 = x,
+ * which is the variation-of-constants sum of Eq. 33 in the variable x.
+ *   x       [P*n], T [P] (>= 0), p_star [P*n]
+ *   x_traj  [P*(S+1)*n]  point-major, then sample, then state
+ *   u_traj  [P*(S+1)*m]  (u_0 is the control at s = 0)
+ */
+int hopf_trajectory(const hopf_problem *prob, const hopf_opts *opts, int P,
+                    const void *x, const void *T, const void *p_star, int S,
+                    void *x_traj, void *u_traj, void *stream);
+
+/* Human-readable name of a per-point status or a return code. */
+const char *hopf_status_string(int code);
+
+/* Message of the most recent failed call on this host thread ("" if none). */
+const char *hopf_last_error(void);
+
+/* Frees the library's device workspace on the current device. */
+int hopf_release_workspace(void);
+
+/* Device time of the phases of the most recent hopf_value call made with
+ * opts->profile set: node-table build and the primal-dual solve kernel, in
+ * milliseconds, measured with CUDA events on the call's stream.  Waits for
+ * the call to finish.  Returns HOPF_EINVAL if no profiled call was made. */
+int hopf_last_profile(double *ms_tables, double *ms_solve);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOPF_GB300_H */

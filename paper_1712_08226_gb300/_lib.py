@@ -1,0 +1,60 @@
+"""ctypes view of include/hopf.h.  Loads the in-tree libhopf_gb300.so."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhopf_gb300.so")
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+P_double = ctypes.POINTER(c_double)
+P_int = ctypes.POINTER(c_int)
+
+
+class HopfProblem(ctypes.Structure):
+    _fields_ = [("n", c_int), ("m", c_int), ("A", P_double), ("B", P_double), ("ctrl_kind", c_int),
+                ("radius", c_double), ("half_widths", P_double), ("W", P_double)]
+
+
+class HopfOpts(ctypes.Structure):
+    _fields_ = [("rule", c_int), ("N", c_int), ("max_iter", c_int), ("gap_every", c_int),
+                ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
+                ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int)]
+
+
+EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",
+           "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile")
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library (once).  Raises if it is missing: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_1712_08226_gb300.build`")
+    lib = ctypes.CDLL(path)
+    PP, PO = ctypes.POINTER(HopfProblem), ctypes.POINTER(HopfOpts)
+    lib.hopf_default_opts.argtypes = [PO]
+    lib.hopf_default_opts.restype = None
+    lib.hopf_value.argtypes = [PP, PO, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hopf_value.restype = c_int
+    lib.hopf_time_to_reach.argtypes = [PP, PO, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_void_p, P_int, c_void_p]
+    lib.hopf_time_to_reach.restype = c_int
+    lib.hopf_trajectory.argtypes = [PP, PO, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                    c_void_p]
+    lib.hopf_trajectory.restype = c_int
+    lib.hopf_status_string.argtypes = [c_int]
+    lib.hopf_status_string.restype = ctypes.c_char_p
+    lib.hopf_last_error.argtypes = []
+    lib.hopf_last_error.restype = ctypes.c_char_p
+    lib.hopf_release_workspace.argtypes = []
+    lib.hopf_release_workspace.restype = c_int
+    lib.hopf_last_profile.argtypes = [P_double, P_double]
+    lib.hopf_last_profile.restype = c_int
+    _lib = lib
+    return lib

@@ -1,0 +1,682 @@
+// C ABI entry points (include/hopf.h): argument checks, workspace, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hopf {
+// host launchers (defined next to their kernels)
+cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                   const double *qd, const double *W, const double *Tv, const int *active,
+                                   int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
+                                   double *out64, float *out32, double *scratch);
+cudaError_t launch_horizons(int count, cudaStream_t s, const void *t, bool t_is_float, double *Tv);
+template <typename R>
+cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
+                                R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
+                                const int *active, cudaStream_t s);
+cudaError_t launch_pdhg_small(int NS, int m, int grid, int threads, size_t smem, cudaStream_t s,
+                              const float *inst, const SolveParams &prm, int ys_stride, const float *x,
+                              const float *p_init, float *phi, float *pstar, float *gap, int *iters,
+                              int *status, int *counter);
+template <typename R>
+cudaError_t launch_ttr_init(int P, cudaStream_t s, const double *inst0, int n, int m, int N, const R *x,
+                            const R *T_lo, const R *T_hi, double t_max, double *lo, double *hi, int *phase,
+                            int *warm, int *st, double *Tfinal);
+cudaError_t launch_ttr_candidates(int P, cudaStream_t s, const double *lo, const double *hi, const int *phase,
+                                  double *cand, int *active);
+template <typename R>
+cudaError_t launch_ttr_update(int P, cudaStream_t s, double t_max, double tol_T, const double *cand,
+                              const int *active, const R *Pv, const R *Dv, const int *sst, double *lo,
+                              double *hi, int *phase, int *warm, int *st, double *Tfinal, int *remaining);
+template <typename R>
+cudaError_t launch_ttr_finish(int P, cudaStream_t s, const int *st, const int *fst, const double *Tfinal,
+                              R *T_star, int *status);
+template <typename R>
+cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                              const double *qd, int n, int m, int ctrl_kind, int P, const R *x, const R *T,
+                              const R *pstar, int S, R *xt, R *ut, double *scratch);
+}  // namespace hopf
+
+using namespace hopf;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t size = 0;
+};
+std::vector<Workspace> g_ws;
+
+// events of the last profiled hopf_value call
+struct Profile {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    int device = -1;
+    bool valid = false;
+} g_prof;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(HOPF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Bump allocator over the device workspace; a first pass with base == nullptr
+// only measures.
+struct Arena {
+    char *base;
+    size_t off = 0;
+    explicit Arena(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int ensure_workspace(size_t bytes, void **out) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1);
+    Workspace &w = g_ws[dev];
+    if (w.size < bytes) {
+        if (w.ptr) {
+            CU(cudaDeviceSynchronize());
+            CU(cudaFree(w.ptr));
+            w.ptr = nullptr;
+            w.size = 0;
+        }
+        size_t want = bytes + bytes / 4 + (1 << 20);
+        if (cudaMalloc(&w.ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            w.ptr = nullptr;
+            return fail(HOPF_ENOMEM, "cudaMalloc of %zu bytes failed", want);
+        }
+        w.size = want;
+    }
+    *out = w.ptr;
+    return HOPF_SUCCESS;
+}
+
+bool all_finite(const double *a, long long count) {
+    for (long long i = 0; i < count; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+// Host-side argument check: W symmetric positive definite (Cholesky).
+bool is_spd(const double *W, int n) {
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (std::fabs(W[i * n + j] - W[j * n + i]) > 1e-12 * (1.0 + std::fabs(W[i * n + j]))) return false;
+    for (int j = 0; j < n; ++j) {
+        double d = W[j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > 0.0)) return false;
+        L[j * n + j] = std::sqrt(d);
+        for (int i = j + 1; i < n; ++i) {
+            double s = W[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = s / L[j * n + j];
+        }
+    }
+    return true;
+}
+
+int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) {
+    if (!pr || !o) return fail(HOPF_EINVAL, "null problem or options");
+    if (pr->n < 1 || pr->m < 1 || pr->n > 4096 || pr->m > 16)
+        return fail(HOPF_EINVAL, "unsupported sizes n=%d m=%d (1<=n<=4096, 1<=m<=16)", pr->n, pr->m);
+    if (!pr->A || !pr->B || !pr->W) return fail(HOPF_EINVAL, "A, B and W are required");
+    if (pr->ctrl_kind != HOPF_BALL && pr->ctrl_kind != HOPF_BOX)
+        return fail(HOPF_EINVAL, "ctrl_kind must be HOPF_BALL or HOPF_BOX");
+    if (pr->ctrl_kind == HOPF_BALL && !(pr->radius > 0.0 && std::isfinite(pr->radius)))
+        return fail(HOPF_EINVAL, "ball radius must be positive and finite");
+    if (pr->ctrl_kind == HOPF_BOX) {
+        if (!pr->half_widths) return fail(HOPF_EINVAL, "box control needs half_widths");
+        for (int c = 0; c < pr->m; ++c)
+            if (!(pr->half_widths[c] > 0.0) || !std::isfinite(pr->half_widths[c]))
+                return fail(HOPF_EINVAL, "half_widths must be positive and finite");
+    }
+    const long long n = pr->n, m = pr->m;
+    if (!all_finite(pr->A, n * n) || !all_finite(pr->B, n * m) || !all_finite(pr->W, n * n))
+        return fail(HOPF_ENONFINITE, "A, B or W has a non-finite entry");
+    if (!is_spd(pr->W, pr->n)) return fail(HOPF_ENOTSPD, "W is not symmetric positive definite");
+    if (o->precision != HOPF_FP64 && o->precision != HOPF_FP32) return fail(HOPF_EINVAL, "bad precision");
+    if (need_solver) {
+        if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID) return fail(HOPF_EINVAL, "bad rule");
+        if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2) || o->N > (1 << 20))
+            return fail(HOPF_EINVAL, "bad node count N=%d", o->N);
+        if (o->max_iter < 0 || o->gap_every < 1) return fail(HOPF_EINVAL, "bad max_iter or gap_every");
+        if (!(o->tau > 0.0) || !(o->sigma_scale > 0.0) || !(o->sigma_scale <= 1.0))
+            return fail(HOPF_EINVAL, "need tau > 0 and 0 < sigma_scale <= 1");
+        if (!(o->tol_gap >= 0.0)) return fail(HOPF_EINVAL, "bad tol_gap");
+    }
+    return HOPF_SUCCESS;
+}
+
+struct Device {
+    int id = 0, sms = 0;
+    size_t smem_optin = 0;
+};
+
+int query_device(Device *d) {
+    CU(cudaGetDevice(&d->id));
+    CU(cudaDeviceGetAttribute(&d->sms, cudaDevAttrMultiProcessorCount, d->id));
+    int v = 0;
+    CU(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->id));
+    d->smem_optin = (size_t)v;
+    return HOPF_SUCCESS;
+}
+
+// Problem matrices on the device (float64), Q diagonal folded separately.
+struct DevProblem {
+    double *A, *B, *q, *W;
+};
+
+template <typename AR>
+DevProblem take_problem(AR &a, int n, int m) {
+    DevProblem d;
+    d.A = a.template take<double>((size_t)n * n);
+    d.B = a.template take<double>((size_t)n * m);
+    d.q = a.template take<double>((size_t)m);
+    d.W = a.template take<double>((size_t)n * n);
+    return d;
+}
+
+int upload_problem(const DevProblem &d, const hopf_problem *pr, cudaStream_t s) {
+    const int n = pr->n, m = pr->m;
+    std::vector<double> q(m);
+    for (int c = 0; c < m; ++c) q[c] = pr->ctrl_kind == HOPF_BALL ? pr->radius : pr->half_widths[c];
+    CU(cudaMemcpyAsync(d.A, pr->A, sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d.B, pr->B, sizeof(double) * n * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d.q, q.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d.W, pr->W, sizeof(double) * n * n, cudaMemcpyHostToDevice, s));
+    // the staging vector q lives until the copy has been issued from pageable
+    // memory, which completes before cudaMemcpyAsync returns for pageable sources
+    return HOPF_SUCCESS;
+}
+
+int table_threads(int n) { return n >= 24 ? 256 : 64; }
+
+// ------------------------------------------------------------ small kernel
+constexpr int SMALL_TPP = 4;
+constexpr int SMALL_MAX_THREADS = 384;
+
+struct SmallPlan {
+    bool ok = false;
+    int NS = 0, pts = 0, threads = 0, ys_stride = 0, grid = 0;
+    size_t smem = 0;
+};
+
+SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
+    SmallPlan sp;
+    if (n > 16 || m > 2) return sp;
+    sp.NS = (n + 1) & ~1;
+    const int KR = (m * sp.NS + 1 + 3) & ~3;
+    int pad = 0;
+    while ((((N + pad) * m) % 32) != ((SMALL_TPP * m) % 32)) ++pad;
+    sp.ys_stride = (N + pad) * m;
+    const size_t fixed = sizeof(float) * ((size_t)N * KR + 3 * sp.NS * sp.NS);
+    const size_t per_pt = sizeof(float) * (size_t)sp.ys_stride;
+    const size_t budget = dev.smem_optin;
+    if (fixed + 8 * per_pt > budget) return sp;
+    int pts = (int)((budget - fixed) / per_pt);
+    pts = std::min(pts, SMALL_MAX_THREADS / SMALL_TPP);
+    pts -= pts % (32 / SMALL_TPP);
+    if (pts < 32 / SMALL_TPP) return sp;
+    sp.pts = pts;
+    sp.threads = pts * SMALL_TPP;
+    sp.smem = fixed + (size_t)pts * per_pt;
+    int want = (P + pts - 1) / pts;
+    sp.grid = std::max(1, std::min(dev.sms, want));
+    sp.ok = true;
+    return sp;
+}
+
+void fill_params(SolveParams &prm, const hopf_problem *pr, const hopf_opts *o, int P) {
+    prm.n = pr->n;
+    prm.m = pr->m;
+    prm.N = o->N;
+    prm.P = P;
+    prm.ctrl_kind = pr->ctrl_kind;
+    prm.max_iter = o->max_iter;
+    prm.gap_every = o->gap_every;
+    prm.warm = 0;
+    prm.sign_mode = 0;
+    prm.inst_stride = 0;
+    prm.tau = o->tau;
+    prm.tol_gap = o->tol_gap;
+    prm.sign_floor = o->precision == HOPF_FP64 ? 1e-13 : 1e-6;
+}
+
+template <typename R>
+int launch_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi, R *pstar,
+                   R *gap, int *iters, int *status, R *Pv, R *Dv, R *y, const int *active,
+                   cudaStream_t s) {
+    CU(launch_pdhg_generic<R>(inst, prm, x, p_init, phi, pstar, gap, iters, status, Pv, Dv, y, active, s));
+    return HOPF_SUCCESS;
+}
+
+int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *o, const double *Tv,
+                  const int *active, int n_inst, double *inst64, float *inst32, double *scratch, int grid,
+                  cudaStream_t s) {
+    CU(launch_build_instances(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
+                              pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch));
+    return HOPF_SUCCESS;
+}
+
+int table_grid(const Device &dev, int n_inst) { return std::max(1, std::min(n_inst, 4 * dev.sms)); }
+
+// --------------------------------------------------------------- hopf_value
+template <typename R>
+int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *t_,
+               int t_stride, const void *pinit_, void *phi_, void *pstar_, void *gap_, int *iters,
+               int *status, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const bool fp32 = o->precision == HOPF_FP32;
+    const int n_inst = t_stride ? P : 1;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    SmallPlan sp;
+    if (fp32 && t_stride == 0) sp = plan_small(dev, n, m, N, P);
+    const int tgrid = table_grid(dev, n_inst);
+    const bool hio = o->host_io != 0;
+
+    auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
+                    R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
+                    int *&ctr) {
+        d = take_problem(a, n, m);
+        Tv = a.template take<double>(n_inst);
+        i64 = a.template take<double>((size_t)n_inst * L.stride);
+        i32 = fp32 ? a.template take<float>((size_t)n_inst * L.stride) : nullptr;
+        tsc = a.template take<double>((size_t)tgrid * table_scratch_doubles(n, m));
+        dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
+        dt = hio ? a.template take<R>((size_t)n_inst) : (R *)t_;
+        dpi = (hio && pinit_) ? a.template take<R>((size_t)P * n) : (R *)pinit_;
+        dphi = hio ? a.template take<R>(P) : (R *)phi_;
+        dps = hio ? a.template take<R>((size_t)P * n) : (R *)pstar_;
+        dgap = hio ? a.template take<R>(P) : (R *)gap_;
+        dit = hio ? a.template take<int>(P) : iters;
+        dst = hio ? a.template take<int>(P) : status;
+        y = sp.ok ? nullptr : a.template take<R>((size_t)P * N * m);
+        ctr = a.template take<int>(4);
+    };
+    DevProblem d;
+    double *Tv, *i64, *tsc;
+    float *i32;
+    R *dx, *dt, *dpi, *dphi, *dps, *dgap, *y;
+    int *dit, *dst, *ctr;
+    Arena meas(nullptr);
+    plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr);
+
+    rc = upload_problem(d, pr, s);
+    if (rc) return rc;
+    if (hio) {
+        CU(cudaMemcpyAsync(dx, x_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dt, t_, sizeof(R) * n_inst, cudaMemcpyHostToDevice, s));
+        if (pinit_) CU(cudaMemcpyAsync(dpi, pinit_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+    }
+    const bool prof = o->profile != 0;
+    if (prof) {
+        if (g_prof.device != dev.id) {
+            for (auto &e : g_prof.ev)
+                if (e) cudaEventDestroy(e);
+            for (auto &e : g_prof.ev) CU(cudaEventCreate(&e));
+            g_prof.device = dev.id;
+        }
+        g_prof.valid = false;
+        CU(cudaEventRecord(g_prof.ev[0], s));
+    }
+    CU(launch_horizons(n_inst, s, dt, fp32, Tv));
+    rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
+    if (rc) return rc;
+
+    if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.warm = pinit_ != nullptr;
+    prm.inst_stride = t_stride ? 1 : 0;
+    const R *inst = fp32 ? (const R *)i32 : (const R *)i64;
+    if (sp.ok) {
+        CU(cudaMemsetAsync(ctr, 0, sizeof(int), s));
+        CU(launch_pdhg_small(sp.NS, m, sp.grid, sp.threads, sp.smem, s, (const float *)inst, prm, sp.ys_stride,
+                             (const float *)dx, (const float *)dpi, (float *)dphi, (float *)dps, (float *)dgap,
+                             dit, dst, ctr));
+    } else {
+        rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
+        if (rc) return rc;
+    }
+    if (prof) {
+        CU(cudaEventRecord(g_prof.ev[2], s));
+        g_prof.valid = true;
+    }
+    if (hio) {
+        CU(cudaMemcpyAsync(phi_, dphi, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(pstar_, dps, sizeof(R) * P * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(gap_, dgap, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(iters, dit, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status, dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return HOPF_SUCCESS;
+}
+
+// ------------------------------------------------------- hopf_time_to_reach
+template <typename R>
+int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *Tlo_,
+             const void *Thi_, const void *pinit_, void *Tstar_, void *pstar_, void *gap_, int *status,
+             int *steps_out, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const bool fp32 = o->precision == HOPF_FP32;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    const int tgrid = table_grid(dev, P);
+    const bool hio = o->host_io != 0;
+    const bool wb = Tlo_ && Thi_;
+
+    struct Bufs {
+        DevProblem d;
+        double *Tz, *inst0, *i64, *tsc, *lo, *hi, *cand, *Tf;
+        float *i32;
+        int *phase, *warm, *st, *act, *sst, *fst, *its, *rem;
+        R *Pv, *Dv, *phi, *gtmp, *ptmp, *y;
+        R *dx, *dlo, *dhi, *dpi, *dTs, *dps, *dgap;
+        int *dst;
+    } b;
+    auto plan = [&](Arena &a) {
+        b.d = take_problem(a, n, m);
+        b.Tz = a.template take<double>(1);
+        b.inst0 = a.template take<double>(L.stride);
+        b.i64 = a.template take<double>((size_t)P * L.stride);
+        b.i32 = fp32 ? a.template take<float>((size_t)P * L.stride) : nullptr;
+        b.tsc = a.template take<double>((size_t)tgrid * table_scratch_doubles(n, m));
+        b.lo = a.template take<double>(P);
+        b.hi = a.template take<double>(P);
+        b.cand = a.template take<double>(P);
+        b.Tf = a.template take<double>(P);
+        b.phase = a.template take<int>(P);
+        b.warm = a.template take<int>(P);
+        b.st = a.template take<int>(P);
+        b.act = a.template take<int>(P);
+        b.sst = a.template take<int>(P);
+        b.fst = a.template take<int>(P);
+        b.its = a.template take<int>(P);
+        b.rem = a.template take<int>(4);
+        b.Pv = a.template take<R>(P);
+        b.Dv = a.template take<R>(P);
+        b.phi = a.template take<R>(P);
+        b.gtmp = a.template take<R>(P);
+        b.ptmp = a.template take<R>((size_t)P * n);
+        b.y = a.template take<R>((size_t)P * N * m);
+        b.dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
+        b.dlo = (hio && wb) ? a.template take<R>(P) : (R *)Tlo_;
+        b.dhi = (hio && wb) ? a.template take<R>(P) : (R *)Thi_;
+        b.dpi = (hio && pinit_) ? a.template take<R>((size_t)P * n) : (R *)pinit_;
+        b.dTs = hio ? a.template take<R>(P) : (R *)Tstar_;
+        b.dps = hio ? a.template take<R>((size_t)P * n) : (R *)pstar_;
+        b.dgap = hio ? a.template take<R>(P) : (R *)gap_;
+        b.dst = hio ? a.template take<int>(P) : status;
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+
+    rc = upload_problem(b.d, pr, s);
+    if (rc) return rc;
+    if (hio) {
+        CU(cudaMemcpyAsync(b.dx, x_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+        if (wb) {
+            CU(cudaMemcpyAsync(b.dlo, Tlo_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(b.dhi, Thi_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
+        }
+        if (pinit_) CU(cudaMemcpyAsync(b.dpi, pinit_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaMemsetAsync(b.Tz, 0, sizeof(double), s));
+    rc = launch_tables(b.d, pr, o, b.Tz, nullptr, 1, b.inst0, nullptr, b.tsc, 1, s);
+    if (rc) return rc;
+    CU(launch_ttr_init<R>(P, s, b.inst0, n, m, N, b.dx, wb ? b.dlo : nullptr, wb ? b.dhi : nullptr, o->t_max,
+                          b.lo, b.hi, b.phase, b.warm, b.st, b.Tf));
+
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.warm = pinit_ != nullptr;
+    prm.inst_stride = 1;
+    const R *inst = fp32 ? (const R *)b.i32 : (const R *)b.i64;
+    int steps = 0;
+    const int max_steps = 256;
+    for (;;) {
+        CU(launch_ttr_candidates(P, s, b.lo, b.hi, b.phase, b.cand, b.act));
+        rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
+        if (rc) return rc;
+        prm.sign_mode = 1;
+        rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
+                               b.act, s);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
+        CU(launch_ttr_update<R>(P, s, o->t_max, o->tol_T, b.cand, b.act, b.Pv, b.Dv, b.sst, b.lo, b.hi, b.phase,
+                                b.warm, b.st, b.Tf, b.rem));
+        int remaining = 0;
+        CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ++steps;
+        if (remaining == 0 || steps >= max_steps) break;
+    }
+    // final certified solve at T* (T = 0 inside the target, t_max if unreachable)
+    rc = launch_tables(b.d, pr, o, b.Tf, nullptr, P, b.i64, b.i32, b.tsc, tgrid, s);
+    if (rc) return rc;
+    prm.sign_mode = 0;
+    rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.dps, b.dgap, b.its, b.fst, b.Pv, b.Dv, b.y,
+                           nullptr, s);
+    if (rc) return rc;
+    CU(launch_ttr_finish<R>(P, s, b.st, b.fst, b.Tf, b.dTs, b.dst));
+    if (hio) {
+        CU(cudaMemcpyAsync(Tstar_, b.dTs, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(pstar_, b.dps, sizeof(R) * P * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(gap_, b.dgap, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status, b.dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    if (steps_out) *steps_out = steps;
+    return HOPF_SUCCESS;
+}
+
+// --------------------------------------------------------- hopf_trajectory
+template <typename R>
+int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *T_,
+              const void *ps_, int S, void *xt_, void *ut_, cudaStream_t s) {
+    const int n = pr->n, m = pr->m;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    const bool hio = o->host_io != 0;
+    const int grid = std::max(1, std::min(P, 4 * dev.sms));
+    const long long per = 5LL * n * n + 4LL * n + 2LL * n * m + 48;
+    DevProblem d;
+    double *sc;
+    R *dx, *dT, *dps, *dxt, *dut;
+    auto plan = [&](Arena &a) {
+        d = take_problem(a, n, m);
+        sc = a.template take<double>((size_t)grid * per);
+        dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
+        dT = hio ? a.template take<R>(P) : (R *)T_;
+        dps = hio ? a.template take<R>((size_t)P * n) : (R *)ps_;
+        dxt = hio ? a.template take<R>((size_t)P * (S + 1) * n) : (R *)xt_;
+        dut = hio ? a.template take<R>((size_t)P * (S + 1) * m) : (R *)ut_;
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    rc = upload_problem(d, pr, s);
+    if (rc) return rc;
+    if (hio) {
+        CU(cudaMemcpyAsync(dx, x_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dT, T_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dps, ps_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+    }
+    CU(launch_trajectory<R>(grid, table_threads(n), s, d.A, d.B, d.q, n, m, pr->ctrl_kind, P, dx, dT, dps, S,
+                            dxt, dut, sc));
+    if (hio) {
+        CU(cudaMemcpyAsync(xt_, dxt, sizeof(R) * P * (S + 1) * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(ut_, dut, sizeof(R) * P * (S + 1) * m, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return HOPF_SUCCESS;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void hopf_default_opts(hopf_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->rule = HOPF_LEFT_RIEMANN;
+    o->N = 100;
+    o->max_iter = 100000;
+    o->gap_every = 8;
+    o->precision = HOPF_FP32;
+    o->host_io = 0;
+    o->tau = 1.0;
+    o->sigma_scale = 1.0;
+    o->tol_gap = 1e-5;
+    o->t_max = 10.0;
+    o->tol_T = 1e-5;
+}
+
+int hopf_value(const hopf_problem *prob, const hopf_opts *opts, int P, const void *x, const void *t,
+               int t_stride, const void *p_init, void *phi, void *p_star, void *gap, int *iters, int *status,
+               void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_problem(prob, opts, true);
+    if (rc) return rc;
+    if (P < 0) return fail(HOPF_EINVAL, "P must be >= 0");
+    if (P == 0) return HOPF_SUCCESS;
+    if (t_stride != 0 && t_stride != 1) return fail(HOPF_EINVAL, "t_stride must be 0 or 1");
+    if (!x || !t || !phi || !p_star || !gap || !iters || !status) return fail(HOPF_EINVAL, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == HOPF_FP64)
+        return value_impl<double>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+    return value_impl<float>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+}
+
+int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P, const void *x, const void *T_lo,
+                       const void *T_hi, const void *p_init, void *T_star, void *p_star, void *gap, int *status,
+                       int *steps, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_problem(prob, opts, true);
+    if (rc) return rc;
+    if (P < 0) return fail(HOPF_EINVAL, "P must be >= 0");
+    if (steps) *steps = 0;
+    if (P == 0) return HOPF_SUCCESS;
+    if (!(opts->t_max > 0.0) || !(opts->tol_T > 0.0)) return fail(HOPF_EINVAL, "need t_max > 0 and tol_T > 0");
+    if ((T_lo == nullptr) != (T_hi == nullptr)) return fail(HOPF_EINVAL, "give both T_lo and T_hi or neither");
+    if (!x || !T_star || !p_star || !gap || !status) return fail(HOPF_EINVAL, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == HOPF_FP64)
+        return ttr_impl<double>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
+    return ttr_impl<float>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
+}
+
+int hopf_trajectory(const hopf_problem *prob, const hopf_opts *opts, int P, const void *x, const void *T,
+                    const void *p_star, int S, void *x_traj, void *u_traj, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_problem(prob, opts, false);
+    if (rc) return rc;
+    if (P < 0 || S < 1) return fail(HOPF_EINVAL, "need P >= 0 and S >= 1");
+    if (P == 0) return HOPF_SUCCESS;
+    if (!x || !T || !p_star || !x_traj || !u_traj) return fail(HOPF_EINVAL, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == HOPF_FP64)
+        return traj_impl<double>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
+    return traj_impl<float>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
+}
+
+const char *hopf_status_string(int code) {
+    switch (code) {
+        case HOPF_OK: return "ok";
+        case HOPF_MAXITER: return "max_iter reached";
+        case HOPF_NONFINITE: return "non-finite iterate";
+        case HOPF_UNREACHABLE: return "target unreachable within t_max";
+        case HOPF_AMBIGUOUS_SIGN: return "sign of phi not certified";
+        case HOPF_EINVAL: return "invalid argument";
+        case HOPF_ENOTSPD: return "W not symmetric positive definite";
+        case HOPF_ECUDA: return "CUDA error";
+        case HOPF_ENOMEM: return "device allocation failed";
+        case HOPF_ENONFINITE: return "non-finite problem data";
+        default: return "unknown";
+    }
+}
+
+const char *hopf_last_error(void) { return g_err.c_str(); }
+
+int hopf_last_profile(double *ms_tables, double *ms_solve) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_prof.valid) return fail(HOPF_EINVAL, "no profiled hopf_value call");
+    CU(cudaEventSynchronize(g_prof.ev[2]));
+    float a = 0.f, b = 0.f;
+    CU(cudaEventElapsedTime(&a, g_prof.ev[0], g_prof.ev[1]));
+    CU(cudaEventElapsedTime(&b, g_prof.ev[1], g_prof.ev[2]));
+    if (ms_tables) *ms_tables = a;
+    if (ms_solve) *ms_solve = b;
+    return HOPF_SUCCESS;
+}
+
+int hopf_release_workspace(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if ((int)g_ws.size() > dev && g_ws[dev].ptr) {
+        CU(cudaDeviceSynchronize());
+        CU(cudaFree(g_ws[dev].ptr));
+        g_ws[dev] = Workspace();
+    }
+    return HOPF_SUCCESS;
+}
+
+}  // extern "C"

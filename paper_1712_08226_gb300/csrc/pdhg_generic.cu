@@ -1,0 +1,235 @@
+// Chambolle-Pock iteration for the discretised generalized Hopf formula,
+// general sizes: one warp per query point, any n, m (<= 16) and N, float64 or
+// float32, one shared node table or one table per point (time-to-reach).
+//
+// Iteration (§III, Eq. 15 with theta = 1, §VI):
+//   y_i   <- Proj_{w_i U}( y_i + sigma K_i pbar )            Eq. 22, Eq. 23
+//   p_new <- S (p - tau sum_i K_i^T y_i + tau x0)             Eq. 37
+//   pbar  <- 2 p_new - p
+// Start (§VI): p = pbar = x0, y = K x0; a warm start p0 uses
+// y_i = w_i argmax_{c in U} <c, K_i p0> instead (the dual point that the
+// optimality condition pairs with p0).
+//
+// Certificate every gap_every iterations: the primal objective of Eq. 18 at
+// pbar, P = pbar^T M pbar / 4 + 1 - <x0, pbar> + sum_i w_i |K_i pbar|_*, and
+// the Fenchel dual D(y) = 1 - (x0 - K^T y)^T V (x0 - K^T y) at the feasible y
+// of the same iteration, so that phi lies in [-P, -D].  K_i pbar is already
+// formed by the dual step (as sigma K_i pbar), so the certificate costs no
+// extra pass over the nodes.  Stop when (P - D)/max(1,|P|,|D|) <= tol_gap, or
+// (time-to-reach) as soon as [-P, -D] excludes zero.
+//
+// Lanes of a warp split the nodes in the dual step and the state components
+// in the K^T y, S and quadratic-form products.  The dual variable y lives in
+// a global scratch array (N m values per point).
+#include "common.cuh"
+
+namespace hopf {
+
+constexpr int GEN_MMAX = 16;
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams prm,
+                                    const R *__restrict__ x, const R *__restrict__ p_init,
+                                    R *__restrict__ phi, R *__restrict__ pstar, R *__restrict__ gap_out,
+                                    int *__restrict__ iters, int *__restrict__ status,
+                                    R *__restrict__ P_out, R *__restrict__ D_out,
+                                    R *__restrict__ y_scratch, const int *__restrict__ active) {
+    const int n = prm.n, m = prm.m, N = prm.N;
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * warps + warp;
+    if (k >= prm.P) return;                       // uniform per warp
+    if (active && !active[k]) return;
+    extern __shared__ unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 6 * n;
+    R *p = sm, *pb = sm + n, *qv = sm + 2 * n, *acc = sm + 3 * n, *x0 = sm + 4 * n, *vt = sm + 5 * n;
+
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    const R *I = inst_base + (prm.inst_stride ? (long long)k * L.stride : 0LL);
+    const R *K = I + L.K, *w = I + L.w, *M = I + L.M, *V = I + L.V, *S = I + L.S, *sc = I + L.sc;
+    const R sigma = sc[SC_SIGMA];
+    const bool zero = sc[SC_ZERO] != R(0);
+    const R tau = (R)prm.tau;
+    R *y = y_scratch + (long long)k * N * m;
+    const bool ball = prm.ctrl_kind == HOPF_BALL;
+
+    for (int j = lane; j < n; j += 32) x0[j] = x[(long long)k * n + j];
+    __syncwarp();
+
+    if (zero) {
+        // T = 0: phi = J_x(x) = x^T V x - 1 (V = W^-1 here), p* = grad J_x = 2 V x
+        R part = 0;
+        for (int j = lane; j < n; j += 32) {
+            R s = 0;
+            for (int l = 0; l < n; ++l) s = fma(V[j * n + l], x0[l], s);
+            pstar[(long long)k * n + j] = R(2) * s;
+            part = fma(x0[j], s, part);
+        }
+        R J = warp_sum(part) - R(1);
+        if (lane == 0) {
+            phi[k] = J;
+            gap_out[k] = 0;
+            iters[k] = 0;
+            status[k] = HOPF_OK;
+            if (P_out) P_out[k] = -J;
+            if (D_out) D_out[k] = -J;
+        }
+        return;
+    }
+
+    for (int j = lane; j < n; j += 32) {
+        R v = prm.warm ? p_init[(long long)k * n + j] : x0[j];
+        p[j] = v;
+        pb[j] = v;
+    }
+    __syncwarp();
+    // y0: K p0 (cold, §VI) or w_i argmax_U <c, K_i p0> (warm)
+    for (int i = lane; i < N; i += 32) {
+        R t[GEN_MMAX];
+        const R *Ki = K + (long long)i * m * n;
+        R nrm2 = 0;
+        for (int c = 0; c < m; ++c) {
+            R s = 0;
+            for (int j = 0; j < n; ++j) s = fma(Ki[c * n + j], p[j], s);
+            t[c] = s;
+            nrm2 = fma(s, s, nrm2);
+        }
+        R wi = w[i];
+        for (int c = 0; c < m; ++c) {
+            R v = t[c];
+            if (prm.warm) {
+                if (ball) v = (nrm2 > R(0)) ? wi * v / sqrt(nrm2) : R(0);
+                else v = (v >= R(0)) ? wi : -wi;
+            }
+            y[(long long)i * m + c] = v;
+        }
+    }
+    __syncwarp();
+
+    const int g = prm.gap_every;
+    auto is_check = [&](int it) { return it >= 2 && (it % g == 0 || it > prm.max_iter); };
+    R Dprev = 0, Pc = 0, Dc = 0, gc = 0;
+    int st = HOPF_MAXITER;
+    int it = 1;
+    for (;; ++it) {
+        const bool check = is_check(it);
+        for (int j = lane; j < n; j += 32) qv[j] = sigma * pb[j];
+        __syncwarp();
+        R hs = 0;
+        for (int i = lane; i < N; i += 32) {
+            R t[GEN_MMAX];
+            const R *Ki = K + (long long)i * m * n;
+            R *yi = y + (long long)i * m;
+            const R wi = w[i];
+            R nt = 0, nu = 0;
+            for (int c = 0; c < m; ++c) {
+                R s = 0;
+                for (int j = 0; j < n; ++j) s = fma(Ki[c * n + j], qv[j], s);
+                nt += ball ? s * s : fabs(s);
+                R u = yi[c] + s;
+                t[c] = u;
+                nu = fma(u, u, nu);
+            }
+            if (check) hs = fma(wi, ball ? sqrt(nt) : nt, hs);
+            if (ball) {
+                R scale = (nu > wi * wi) ? wi / sqrt(nu) : R(1);
+                for (int c = 0; c < m; ++c) yi[c] = t[c] * scale;
+            } else {
+                for (int c = 0; c < m; ++c) yi[c] = fmin(fmax(t[c], -wi), wi);
+            }
+        }
+        if (check) {
+            hs = warp_sum(hs);
+            R H = (sigma > R(0)) ? hs / sigma : R(0);
+            R part = 0;
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(M[j * n + l], pb[l], s);
+                part += pb[j] * (R(0.25) * s - x0[j]);
+            }
+            Pc = warp_sum(part) + R(1) + H;
+            Dc = Dprev;
+            gc = rel_gap(Pc, Dc);
+            if (!isfinite(Pc) || !isfinite(Dc)) { st = HOPF_NONFINITE; break; }
+            bool conv = gc <= (R)prm.tol_gap;
+            if (prm.sign_mode) conv = conv || Pc < R(0) || Dc > R(0) || gc <= (R)prm.sign_floor;
+            if (conv) { st = HOPF_OK; break; }
+            if (it > prm.max_iter) { st = HOPF_MAXITER; break; }
+        }
+        __syncwarp();
+        // K^T y: lanes over state components, sum over nodes
+        for (int j = lane; j < n; j += 32) {
+            R s = 0;
+            for (int i = 0; i < N; ++i) {
+                const R *Ki = K + (long long)i * m * n;
+                const R *yi = y + (long long)i * m;
+                for (int c = 0; c < m; ++c) s = fma(Ki[c * n + j], yi[c], s);
+            }
+            acc[j] = s;
+            vt[j] = p[j] - tau * s + tau * x0[j];
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            R s = 0;
+            for (int l = 0; l < n; ++l) s = fma(S[j * n + l], vt[l], s);
+            pb[j] = R(2) * s - p[j];
+            p[j] = s;
+        }
+        __syncwarp();
+        if (is_check(it + 1)) {
+            for (int j = lane; j < n; j += 32) vt[j] = x0[j] - acc[j];
+            __syncwarp();
+            R part = 0;
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(V[j * n + l], vt[l], s);
+                part = fma(vt[j], s, part);
+            }
+            Dprev = R(1) - warp_sum(part);
+            __syncwarp();
+        }
+    }
+    for (int j = lane; j < n; j += 32) pstar[(long long)k * n + j] = pb[j];
+    if (lane == 0) {
+        phi[k] = -Pc;
+        gap_out[k] = gc;
+        iters[k] = it - 1;
+        status[k] = st;
+        if (P_out) P_out[k] = Pc;
+        if (D_out) D_out[k] = Dc;
+    }
+}
+
+template <typename R>
+cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
+                                R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
+                                const int *active, cudaStream_t s) {
+    constexpr int warps = 4;
+    const int threads = warps * 32;
+    const int grid = (prm.P + warps - 1) / warps;
+    const size_t smem = (size_t)warps * 6 * prm.n * sizeof(R);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(pdhg_generic_kernel<R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    pdhg_generic_kernel<R><<<grid, threads, smem, s>>>(inst, prm, x, p_init, phi, pstar, gap, iters, status,
+                                                       Pv, Dv, y, active);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_pdhg_generic<double>(const double *, const SolveParams &, const double *,
+                                                 const double *, double *, double *, double *, int *, int *,
+                                                 double *, double *, double *, const int *, cudaStream_t);
+template cudaError_t launch_pdhg_generic<float>(const float *, const SolveParams &, const float *,
+                                                const float *, float *, float *, float *, int *, int *, float *,
+                                                float *, float *, const int *, cudaStream_t);
+
+}  // namespace hopf

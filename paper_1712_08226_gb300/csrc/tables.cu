@@ -1,0 +1,136 @@
+// Node tables of the discretised generalized Hopf formula, built on the
+// device in float64 (one thread block per horizon T).
+//
+// For horizon T and N nodes the quadrature of §III.A gives node times t_i and
+// weights w_i (left Riemann, Eq. 17: t_i = i T/N, w_i = T/N; trapezoid:
+// t_i = i T/(N-1), end weights halved).  The node matrices of Eq. 20,
+//   K_i = (-e^{-s_i A} B Q)^T,   s_i = T - t_i,
+// are generated without one exponential per node: with h the node spacing,
+// s_i = k h for an integer k, so e^{-s_i A} B Q = (e^{-hA})^k B Q is obtained
+// by repeated multiplication with E_h = e^{-hA} (the paper evaluates the same
+// products with the Al-Mohy-Higham action of the exponential; §III.A and §VI).
+// The same pass accumulates the Gram matrix sum_i K_i^T K_i, whose largest
+// eigenvalue is |K|^2 for the dual step sigma = 1/(tau |K|^2) of §VI.
+// The quadratic target of §VI.A needs M = V(0)^-1 = e^{-TA} W e^{-TA^T}
+// (Eq. 35), V = M^-1 and the prox matrix S = (I + tau M/2)^-1 (Eq. 37).
+#include "common.cuh"
+#include "cta_linalg.cuh"
+
+namespace hopf {
+
+__global__ void build_instances_kernel(const double *__restrict__ A, const double *__restrict__ B,
+                                       const double *__restrict__ qd, const double *__restrict__ W,
+                                       const double *__restrict__ Tv, const int *__restrict__ active,
+                                       int n_inst, int n, int m, int N, int rule, double tau,
+                                       double sigma_scale, double *out64, float *out32,
+                                       double *scratch) {
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    double *sc = scratch + (long long)blockIdx.x * table_scratch_doubles(n, m);
+    double *X = sc, *T1 = X + n * n, *Eh = T1 + n * n, *ET = Eh + n * n, *T2 = ET + n * n;
+    double *C = T2 + n * n, *Aug = C + n * n;             // Aug: 2 n^2
+    double *Ga = Aug + 2 * n * n, *Gb = Ga + n * m;
+    double *v = Gb + n * m, *u = v + n;
+    double *red = u + n;                                  // 8 doubles
+    int *piv = (int *)(red + 8);
+
+    for (int inst = blockIdx.x; inst < n_inst; inst += gridDim.x) {
+        if (active && !active[inst]) continue;
+        const double T = Tv[inst];
+        double *o = out64 + (long long)inst * L.stride;
+        const double h = (rule == HOPF_TRAPEZOID) ? T / (double)(N - 1) : T / (double)N;
+
+        cta::expm(Eh, A, -h, n, X, T1, red);
+        // G = B Q, Gram accumulator C = 0
+        for (int e = threadIdx.x; e < n * m; e += blockDim.x) Ga[e] = B[e] * qd[e % m];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) C[e] = 0.0;
+        __syncthreads();
+        double *cur = Ga, *nxt = Gb;
+        for (int idx = 0; idx < N; ++idx) {
+            if (rule != HOPF_TRAPEZOID || idx > 0) {
+                cta::matmul(nxt, Eh, cur, n, n, m);     // advance s by h
+                double *t = cur; cur = nxt; nxt = t;
+            }
+            const int i = N - 1 - idx;                  // node with s_i = (idx + [left]) h
+            double *Ki = o + L.K + (long long)i * m * n;
+            for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+                int c = e / n, j = e % n;
+                Ki[e] = -cur[j * m + c];
+            }
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                int a = e / n, b = e % n;
+                double s = 0.0;
+                for (int c = 0; c < m; ++c) s = fma(cur[a * m + c], cur[b * m + c], s);
+                C[e] += s;
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            double wi = h;
+            if (rule == HOPF_TRAPEZOID && (i == 0 || i == N - 1)) wi = 0.5 * h;
+            o[L.w + i] = wi;
+        }
+        // M = e^{-TA} W e^{-TA}^T (symmetrised), V = M^-1, S = (I + tau M / 2)^-1
+        cta::expm(ET, A, -T, n, X, T1, red);
+        cta::matmul(T2, ET, W, n, n, n);
+        cta::matmul_bt(T1, T2, ET, n, n, n);
+        double *Mo = o + L.M, *Vo = o + L.V, *So = o + L.S;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int a = e / n, b = e % n;
+            Mo[e] = 0.5 * (T1[a * n + b] + T1[b * n + a]);
+        }
+        __syncthreads();
+        bool okV = cta::invert(T2, Mo, n, Aug, piv, red);
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int a = e / n, b = e % n;
+            Vo[e] = okV ? 0.5 * (T2[a * n + b] + T2[b * n + a]) : __longlong_as_double(0x7ff8000000000000LL);
+        }
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+            X[e] = ((e / n == e % n) ? 1.0 : 0.0) + 0.5 * tau * Mo[e];
+        __syncthreads();
+        bool okS = cta::invert(T2, X, n, Aug, piv, red);
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+            So[e] = okS ? T2[e] : __longlong_as_double(0x7ff8000000000000LL);
+        __syncthreads();
+        double L2 = cta::lambda_max(C, n, v, u, red);
+        if (threadIdx.x == 0) {
+            double *s = o + L.sc;
+            s[SC_SIGMA] = (L2 > 0.0) ? sigma_scale / (tau * L2) : 0.0;
+            s[SC_T] = T;
+            s[SC_L2] = L2;
+            s[SC_ZERO] = (T == 0.0) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (out32) {
+            float *f = out32 + (long long)inst * L.stride;
+            for (long long e = threadIdx.x; e < L.stride; e += blockDim.x) f[e] = (float)o[e];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void to_double_kernel(const float *src, double *dst, int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = (double)src[i];
+}
+
+__global__ void copy_double_kernel(const double *src, double *dst, int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = src[i];
+}
+
+cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                   const double *qd, const double *W, const double *Tv, const int *active,
+                                   int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
+                                   double *out64, float *out32, double *scratch) {
+    build_instances_kernel<<<grid, threads, 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule, tau,
+                                                    sigma_scale, out64, out32, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_horizons(int count, cudaStream_t s, const void *t, bool t_is_float, double *Tv) {
+    if (t_is_float) to_double_kernel<<<(count + 255) / 256, 256, 0, s>>>((const float *)t, Tv, count);
+    else copy_double_kernel<<<(count + 255) / 256, 256, 0, s>>>((const double *)t, Tv, count);
+    return cudaGetLastError();
+}
+
+}  // namespace hopf

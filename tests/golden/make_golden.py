@@ -1,0 +1,82 @@
+"""Writes the stored expected values used by the GPU parity tests.
+
+Every number here comes from the FP64 oracle (oracle/), run on the seeded
+inputs of inputs/workloads.py; nothing is read back from the CUDA path.
+Run from the repository root:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from inputs import workloads as wl  # noqa: E402
+from oracle import hopf as oh  # noqa: E402
+
+OUT = os.path.dirname(os.path.abspath(__file__))
+
+
+def dump(name, meta, **arrays):
+    doc = dict(meta=meta, **{k: np.asarray(v).tolist() for k, v in arrays.items()})
+    with open(os.path.join(OUT, name), "w") as f:
+        json.dump(doc, f, separators=(",", ":"))
+    print("wrote", name)
+
+
+def random10_values(P=320):
+    w = wl.workload_random10(P)
+    r = oh.value(w["system"], w["x"], w["t"], w["N"], w["rule"], tau=w["tau"], tol=1e-10,
+                 max_iter=400000)
+    assert np.all(r["status"] == oh.OK)
+    dump("random10_values.json",
+         dict(source="oracle.hopf.value", workload="random_n10_m2 (seed 1), x~N(0,4I) seed 2, first P points",
+              P=P, t=w["t"], N=w["N"], rule="left_riemann", tau=w["tau"], oracle_tol=1e-10),
+         phi=r["phi"], p=r["p"], gap=r["gap"])
+
+
+def di_values(P=64):
+    w = wl.workload_di(P)
+    T = 1.5
+    r = oh.value(w["system"], w["x"], T, w["N"], w["rule"], tau=w["tau"], tol=1e-12, max_iter=400000)
+    assert np.all(r["status"] == oh.OK)
+    dump("di_values_T1.5.json",
+         dict(source="oracle.hopf.value", workload="double integrator, r=0.1, x~U[-2,2]^2 seed 0",
+              P=P, T=T, N=w["N"], rule="trapezoid", tau=w["tau"], oracle_tol=1e-12),
+         phi=r["phi"], p=r["p"])
+
+
+def di_time_to_reach(P=64):
+    w = wl.workload_di(P)
+    r = oh.time_to_reach(w["system"], w["x"], w["t_max"], w["N"], w["rule"], tau=w["tau"],
+                         tol_T=1e-8, tol_gap=1e-10)
+    dump("di_time_to_reach.json",
+         dict(source="oracle.hopf.time_to_reach", workload="double integrator, r=0.1, x~U[-2,2]^2 seed 0",
+              P=P, t_max=w["t_max"], N=w["N"], rule="trapezoid", tau=w["tau"], oracle_tol_T=1e-8),
+         T=r["T"], p=r["p"], status=r["status"])
+
+
+def box_values(P=200):
+    # small-state box-control system (m = 1): chain of 2 masses, 4 states
+    sysd = wl.spring_chain(masses=2, actuators=1, radius_target=0.5)
+    x = wl.normal_points(31, P, 4, 1.0)
+    r = oh.value(sysd, x, 1.7, 64, oh.LEFT_RIEMANN, tau=0.5, tol=1e-10, max_iter=400000)
+    assert np.all(r["status"] == oh.OK)
+    dump("chain2_box_values.json",
+         dict(source="oracle.hopf.value", workload="2-mass spring chain (n=4, m=1 box), x~N(0,I) seed 31",
+              P=P, T=1.7, N=64, rule="left_riemann", tau=0.5, oracle_tol=1e-10),
+         x=x, phi=r["phi"], p=r["p"])
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["random10", "di", "ttr", "box"]
+    if "box" in which:
+        box_values()
+    if "di" in which:
+        di_values()
+    if "ttr" in which:
+        di_time_to_reach()
+    if "random10" in which:
+        random10_values()

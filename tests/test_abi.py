@@ -1,0 +1,102 @@
+"""The C ABI library builds, loads without a GPU, exports every entry point
+declared in include/hopf.h, and rejects bad arguments before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_08226_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hopf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hopf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "hopf_value" in names and "hopf_time_to_reach" in names and "hopf_trajectory" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_1712_08226_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_functions()
+
+
+def test_struct_layout_matches_header():
+    # field order and types of the ctypes mirror follow the header's structs
+    from paper_1712_08226_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "hopf.h")).read()
+    for cname, py in (("hopf_problem", _lib.HopfProblem), ("hopf_opts", _lib.HopfOpts)):
+        body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + cname + ";", src, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"([A-Za-z_]+)\s*;", re.sub(r"\*", " ", body))
+        assert fields == [f[0] for f in py._fields_], (cname, fields)
+
+
+def test_default_opts(lib):
+    from paper_1712_08226_gb300 import _lib
+    o = _lib.HopfOpts()
+    lib.hopf_default_opts(ctypes.byref(o))
+    assert o.N == 100 and o.gap_every == 8 and o.sigma_scale == 1.0 and o.tol_gap == 1e-5
+
+
+def _call_value(lib, sysd, opts_kw=None, P=4):
+    from paper_1712_08226_gb300 import api
+    s = api.System.from_dict(sysd)
+    opts = api.Options(**(opts_kw or {}))
+    prob = s.c_struct()
+    o = opts.c_struct(True)
+    x = np.zeros((P, s.n), np.float32)
+    t = np.ones(1, np.float32)
+    outs = [np.zeros(P, np.float32), np.zeros((P, s.n), np.float32), np.zeros(P, np.float32),
+            np.zeros(P, np.int32), np.zeros(P, np.int32)]
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    return lib.hopf_value(ctypes.byref(prob), ctypes.byref(o), P, vp(x), vp(t), 0, None,
+                          *[vp(a) for a in outs], None)
+
+
+def test_rejects_non_spd_target(lib):
+    from inputs import workloads as wl
+    sysd = wl.double_integrator(0.1)
+    sysd["W"] = np.array([[1.0, 2.0], [2.0, 1.0]])
+    assert _call_value(lib, sysd) == -2
+    assert b"positive definite" in lib.hopf_last_error()
+
+
+def test_rejects_non_finite_and_bad_options(lib):
+    from inputs import workloads as wl
+    sysd = wl.double_integrator(0.1)
+    bad = dict(sysd)
+    bad["A"] = np.array([[0.0, np.nan], [0.0, 0.0]])
+    assert _call_value(lib, bad) == -5
+    assert _call_value(lib, sysd, dict(tau=-1.0)) == -1
+    assert _call_value(lib, sysd, dict(N=1, rule=1)) == -1
+    assert _call_value(lib, sysd, dict(sigma_scale=1.5)) == -1
+    assert _call_value(lib, sysd, dict(gap_every=0)) == -1
+    neg_box = dict(sysd)
+    neg_box["half_widths"] = np.array([-1.0])
+    assert _call_value(lib, neg_box) == -1
+
+
+def test_empty_batch_needs_no_device(lib):
+    from inputs import workloads as wl
+    assert _call_value(lib, wl.double_integrator(0.1), P=0) == 0
+
+
+def test_status_strings(lib):
+    assert lib.hopf_status_string(0) == b"ok"
+    assert lib.hopf_status_string(3).startswith(b"target unreachable")
+    assert lib.hopf_status_string(-2).startswith(b"W not")

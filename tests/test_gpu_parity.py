@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Stored expected values under tests/golden/ were written by
+tests/golden/make_golden.py, which calls only the oracle.  Tolerances:
+value |phi_gpu - phi| <= 1e-5 max(1, |phi|) for float32 and tighter for
+float64; time-to-reach |T_gpu - T| <= 1e-4 T; trajectory end point <= 1e-4.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from inputs import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1712_08226_gb300 as H
+    from paper_1712_08226_gb300 import build
+    build.build()
+    H._lib.load()
+    return H
+
+
+def cuda(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.asarray(a), dtype=dtype or torch.float32, device="cuda")
+
+
+def np_(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_err(a, b):
+    return np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+
+# ------------------------------------------------------------------ values
+def test_random10_value_small_kernel_fp32(H):
+    g = gold("random10_values.json")
+    P = g["meta"]["P"]
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], tau=w["tau"], tol_gap=1e-5, precision=H.FP32)
+    r = H.value(sysd, cuda(w["x"]), w["t"], opts)
+    st = r["status"].cpu().numpy()
+    assert np.all(st == 0), np.unique(st, return_counts=True)
+    assert np_(r["gap"]).max() <= 1e-5
+    err = rel_err(np_(r["phi"]), np.array(g["phi"]))
+    assert err.max() <= 1e-5, (err.max(), np.argmax(err))
+    pe = np.linalg.norm(np_(r["p"]) - np.array(g["p"]), axis=1) / np.maximum(1, np.linalg.norm(g["p"], axis=1))
+    assert pe.max() < 5e-2
+
+
+def test_random10_value_generic_fp32_per_point_horizon(H):
+    g = gold("random10_values.json")
+    P = 70
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], tau=w["tau"], tol_gap=1e-5, precision=H.FP32)
+    r = H.value(sysd, cuda(w["x"]), cuda(np.full(P, w["t"])), opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"][:P]))
+    assert err.max() <= 1e-5, err.max()
+
+
+def test_random10_value_fp64(H):
+    import torch
+    g = gold("random10_values.json")
+    P = 48
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], tau=w["tau"], tol_gap=1e-9, precision=H.FP64, max_iter=400000)
+    r = H.value(sysd, cuda(w["x"], torch.float64), w["t"], opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"][:P]))
+    assert err.max() <= 2e-9, err.max()
+
+
+def test_di_value_fp64_trapezoid_box(H):
+    import torch
+    g = gold("di_values_T1.5.json")
+    w = wl.workload_di(g["meta"]["P"])
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], rule=H.TRAPEZOID, tau=w["tau"], tol_gap=1e-11, precision=H.FP64,
+                     max_iter=1000000)
+    r = H.value(sysd, cuda(w["x"], torch.float64), g["meta"]["T"], opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"]))
+    assert err.max() <= 1e-9, err.max()
+
+
+def test_chain_box_small_kernel_m1(H):
+    g = gold("chain2_box_values.json")
+    m = g["meta"]
+    sysd = H.System.from_dict(wl.spring_chain(masses=2, actuators=1, radius_target=0.5))
+    opts = H.Options(N=m["N"], tau=m["tau"], tol_gap=1e-5, precision=H.FP32)
+    r = H.value(sysd, cuda(g["x"]), m["T"], opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"]))
+    assert err.max() <= 1e-5, err.max()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_single_integrator_closed_form(H, kind):
+    # A = 0, B = I: phi = max(|x| - rho T, 0)^2/r^2 - 1 (ball) or the
+    # soft-threshold form (box), exactly for any quadrature (basic Hopf formula).
+    n, rho, r, T = 3, 0.8, 0.5, 0.9
+    sysd = H.System.from_dict(wl.single_integrator(n, kind, radius=rho, radius_target=r))
+    x = wl.normal_points(7, 40, n, 1.5)
+    opts = H.Options(N=16, tau=1.0, tol_gap=1e-10, precision=H.FP64)
+    import torch
+    res = H.value(sysd, cuda(x, torch.float64), T, opts)
+    if kind == 0:
+        exact = np.maximum(np.linalg.norm(x, axis=1) - rho * T, 0.0) ** 2 / r ** 2 - 1.0
+    else:
+        exact = np.sum((np.sign(x) * np.maximum(np.abs(x) - rho * T, 0.0)) ** 2, axis=1) / r ** 2 - 1.0
+    assert np.allclose(np_(res["phi"]), exact, rtol=1e-9, atol=1e-9)
+
+
+def test_zero_horizon_is_terminal_cost(H):
+    w = wl.workload_random10(33)
+    sysd = H.System.from_dict(w["system"])
+    r = H.value(sysd, cuda(w["x"]), 0.0, H.Options(N=256, tau=0.15))
+    Wi = np.linalg.inv(w["system"]["W"])
+    J = np.einsum("pi,ij,pj->p", w["x"], Wi, w["x"]) - 1.0
+    assert np.allclose(np_(r["phi"]), J, rtol=1e-5)
+    assert np.allclose(np_(r["p"]), 2 * w["x"] @ Wi.T, rtol=1e-5, atol=1e-5)
+
+
+def test_empty_batch(H):
+    w = wl.workload_random10(1)
+    sysd = H.System.from_dict(w["system"])
+    r = H.value(sysd, cuda(np.zeros((0, 10))), 2.0, H.Options(N=256))
+    assert r["phi"].numel() == 0
+
+
+def test_host_io_matches_device(H):
+    w = wl.workload_random10(100)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=256, tau=0.15)
+    rd = H.value(sysd, cuda(w["x"]), 2.0, opts)
+    rh = H.value(sysd, w["x"].astype(np.float32), 2.0, opts)
+    assert np.array_equal(np_(rd["phi"]), rh["phi"].astype(np.float64))
+    assert np.array_equal(rd["iters"].cpu().numpy(), rh["iters"])
+
+
+def test_warm_start_from_exact_dual_converges_fast(H):
+    g = gold("random10_values.json")
+    P = 64
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=256, tau=w["tau"])
+    cold = H.value(sysd, cuda(w["x"]), 2.0, opts)
+    warm = H.value(sysd, cuda(w["x"]), 2.0, opts, p_init=cuda(np.array(g["p"][:P])))
+    assert np.all(warm["status"].cpu().numpy() == 0)
+    assert warm["iters"].float().mean() < 0.5 * cold["iters"].float().mean()
+    assert rel_err(np_(warm["phi"]), np.array(g["phi"][:P])).max() <= 1e-5
+
+
+def test_ragged_node_count_against_oracle(H):
+    from oracle import hopf as oh
+    w = wl.workload_random10(24)
+    N = 250                                   # not a multiple of the node split
+    ref = oh.value(w["system"], w["x"], 1.3, N, oh.LEFT_RIEMANN, tau=0.15, tol=1e-10, max_iter=400000)
+    sysd = H.System.from_dict(w["system"])
+    r = H.value(sysd, cuda(w["x"]), 1.3, H.Options(N=N, tau=0.15))
+    assert np.all(r["status"].cpu().numpy() == 0)
+    assert rel_err(np_(r["phi"]), ref["phi"]).max() <= 1e-5
+
+
+def test_full_size_sampled_against_oracle(H):
+    # the benchmark configuration (65,536 points, one launch), checked on a sample
+    from oracle import hopf as oh
+    w = wl.workload_random10(65536)
+    sysd = H.System.from_dict(w["system"])
+    r = H.value(sysd, cuda(w["x"]), w["t"], H.Options(N=w["N"], tau=w["tau"], tol_gap=1e-5))
+    st = r["status"].cpu().numpy()
+    assert np.all(st == 0), np.unique(st, return_counts=True)
+    idx = np.random.default_rng(5).choice(65536, 24, replace=False)
+    ref = oh.value(w["system"], w["x"][idx], w["t"], w["N"], oh.LEFT_RIEMANN, tau=w["tau"], tol=1e-10,
+                   max_iter=400000)
+    assert rel_err(np_(r["phi"])[idx], ref["phi"]).max() <= 1e-5
+
+
+# ------------------------------------------------------------ time to reach
+def test_di_time_to_reach_fp64(H):
+    import torch
+    g = gold("di_time_to_reach.json")
+    m = g["meta"]
+    w = wl.workload_di(m["P"])
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=m["N"], rule=H.TRAPEZOID, tau=m["tau"], tol_gap=1e-8, precision=H.FP64, t_max=m["t_max"],
+                     tol_T=1e-6, max_iter=1000000)
+    r = H.time_to_reach(sysd, cuda(w["x"], torch.float64), opts)
+    T = np_(r["T"])
+    Tg = np.array(g["T"])
+    st = r["status"].cpu().numpy()
+    assert np.all((st == 0) | (st == 4)), np.unique(st, return_counts=True)
+    assert np.all(np.abs(T - Tg) <= 1e-4 * np.maximum(Tg, 1e-3)), np.max(np.abs(T - Tg) / Tg)
+
+
+def test_single_integrator_time_to_reach_fp32(H):
+    n, r = 2, 0.5
+    sysd = H.System.from_dict(wl.single_integrator(n, 0, radius=1.0, radius_target=r))
+    x = np.array([[1.5, 0.2], [0.1, 0.2], [-2.0, 2.5], [3.0, -1.0]])
+    opts = H.Options(N=8, tau=1.0, t_max=6.0, tol_T=1e-6, tol_gap=1e-6)
+    res = H.time_to_reach(sysd, cuda(x), opts)
+    exact = np.maximum(np.linalg.norm(x, axis=1) - r, 0.0)
+    assert np.allclose(np_(res["T"]), exact, rtol=1e-4, atol=1e-6)
+    # an unreachable horizon
+    opts.t_max = 1.0
+    res = H.time_to_reach(sysd, cuda(x), opts)
+    st = res["status"].cpu().numpy()
+    assert st[1] == 0 and st[2] == 3 and st[3] == 3
+
+
+# --------------------------------------------------------------- trajectory
+def test_trajectory_matches_oracle_fp64(H):
+    import torch
+    from oracle import hopf as oh
+    g = gold("di_time_to_reach.json")
+    w = wl.workload_di(g["meta"]["P"])
+    idx = [0, 5, 17, 40]
+    x = w["x"][idx]
+    T = np.array(g["T"])[idx]
+    p = np.array(g["p"])[idx]
+    S = 200
+    sysd = H.System.from_dict(w["system"])
+    r = H.trajectory(sysd, cuda(x, torch.float64), cuda(T, torch.float64), cuda(p, torch.float64), S,
+                     H.Options(precision=H.FP64))
+    xt = np_(r["x"])
+    for k in range(len(idx)):
+        xs, us = oh.trajectory(w["system"], x[k], T[k], p[k], S)
+        assert np.linalg.norm(xt[k, -1] - xs[-1]) <= 1e-4
+        assert np.max(np.abs(xt[k] - xs)) <= 1e-6
+        assert np.allclose(np_(r["u"])[k], us)
