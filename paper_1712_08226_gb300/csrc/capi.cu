@@ -528,7 +528,7 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     if (rc) return rc;
     const bool hio = o->host_io != 0;
     const int grid = std::max(1, std::min(P, 4 * dev.sms));
-    const long long per = 5LL * n * n + 4LL * n + 2LL * n * m + 48;
+    const long long per = 5LL * n * n + 4LL * n + 4LL * n * m + 48;
     DevProblem d;
     double *sc;
     R *dx, *dT, *dps, *dxt, *dut;

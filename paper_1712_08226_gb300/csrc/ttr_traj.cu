@@ -125,7 +125,7 @@ __global__ void trajectory_kernel(const double *__restrict__ A, const double *__
                                   const R *__restrict__ x, const R *__restrict__ T,
                                   const R *__restrict__ pstar, int S, R *__restrict__ xt,
                                   R *__restrict__ ut, double *scratch) {
-    double *sc = scratch + (long long)blockIdx.x * (5LL * n * n + 4LL * n + 2LL * n * m + 48);
+    double *sc = scratch + (long long)blockIdx.x * (5LL * n * n + 4LL * n + 4LL * n * m + 48);
     double *X = sc, *T1 = X + n * n, *Eh = T1 + n * n, *G = Eh + n * n, *BQ = G + n * n;
     double *xs = BQ + n * m, *lam = xs + n, *tmp = lam + n, *tmp2 = tmp + n, *gv = tmp2 + n;
     double *red = gv + 2 * n * m;   // >= 8 doubles
