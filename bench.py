@@ -31,6 +31,7 @@ from inputs import workloads as wl  # noqa: E402
 METRIC = "Hopf solves/sec at gap<=1e-5: warm-start batched vs plain cold PDHG, same GB300"
 POINTS = 65536
 TOL = 1e-5
+TAU_ACCEL = 2.0
 
 
 def rank_env():
@@ -38,9 +39,9 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def workload(rank):
+def workload(rank, points=POINTS):
     # rank r solves its own seeded points; rank 0 is the standard point set
-    w = wl.workload_random10(POINTS, seed_sys=1, seed_pts=2 + 1000 * rank)
+    w = wl.workload_random10(points, seed_sys=1, seed_pts=2 + 1000 * rank)
     return w
 
 
@@ -121,7 +122,7 @@ def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
         return
-    sample = 24
+    sample = 96
     times, ok_total, t_all = [], 0, 0.0
     for step in range(args.warmup + args.steps):
         v, d = cpu_oracle_sample(sample)
@@ -150,6 +151,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=POINTS, help="points per GPU (smaller cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain (Eq. 15) comparison run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -159,7 +163,7 @@ def main():
     # CPU baseline first (fresh single-threaded process, before any CUDA work)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = 48
+        sample = 1024
         v, d = cpu_oracle_sample(sample)
         cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"FP64 numpy oracle, 1 thread, first {sample} of the {POINTS} points, gap<=1e-5, "
@@ -179,11 +183,16 @@ def main():
         dist.barrier()
     H._lib.load()
 
-    w = workload(rank)
+    points = args.points
+    w = workload(rank, points)
     sysd = H.System.from_dict(w["system"])
     n, m, N = 10, 2, w["N"]
-    opts = H.Options(N=N, rule=H.LEFT_RIEMANN, tau=w["tau"], tol_gap=TOL, max_iter=100000, gap_every=8,
-                     precision=H.FP32, profile=True)
+    # cold start, accelerated primal-dual steps (strongly convex G), tau0 = 2
+    opts = H.Options(N=N, rule=H.LEFT_RIEMANN, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8,
+                     precision=H.FP32, profile=True, accel=True)
+    # the paper's iteration (Eq. 15, theta = 1) from the same cold start
+    opts_plain = H.Options(N=N, rule=H.LEFT_RIEMANN, tau=w["tau"], tol_gap=TOL, max_iter=100000, gap_every=8,
+                           precision=H.FP32, profile=True, accel=False)
     x_dev = torch.tensor(w["x"], dtype=torch.float32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
@@ -192,27 +201,41 @@ def main():
         H.value(sysd, x_dev, w["t"], opts)
     torch.cuda.synchronize()
 
+    def timed(o, steps):
+        """Device time per step (CUDA events on the launching stream), L2 flushed before each."""
+        ms, sv, tb, un, okc, iters_all = [], [], [], 0, 0, None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = H.value(sysd, x_dev, w["t"], o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            a, b_ = H.last_profile()
+            tb.append(a)
+            sv.append(b_)
+            it = r["iters"].to(torch.int64)
+            un += int((it + 1).sum().item())
+            okc += int((r["status"] == 0).sum().item())
+            iters_all = it.cpu().numpy()
+        return ms, sv, tb, un, okc, iters_all
+
+    plain = None
+    if not args.no_plain:
+        H.value(sysd, x_dev, w["t"], opts_plain)
+        pm, psv, _, pun, pok, pit = timed(opts_plain, max(1, min(3, args.steps)))
+        plain = {"solves_per_s": pok / len(pm) / (statistics.mean(pm) * 1e-3), "ms_per_step": statistics.mean(pm),
+                 "tau": w["tau"], "mean_iters": float(pit.mean()), "max_iters": int(pit.max()),
+                 "steps": len(pm)}
+
     clocks = ClockSampler(local)
-    step_ms, solve_ms, table_ms, units, ok = [], [], [], 0, 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    for _ in range(args.steps):
-        flush.zero_()                       # L2 flush between timed steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = H.value(sysd, x_dev, w["t"], opts)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        tb, sv = H.last_profile()
-        table_ms.append(tb)
-        solve_ms.append(sv)
-        it = r["iters"].to(torch.int64)
-        units += int((it + 1).sum().item())
-        ok += int((r["status"] == 0).sum().item())
+    step_ms, solve_ms, table_ms, units, ok, iters_last = timed(opts, args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist:
@@ -221,16 +244,19 @@ def main():
     # end to end through the C ABI with host buffers (pinned), copies included
     x_pin = torch.tensor(w["x"], dtype=torch.float32).pin_memory()
     x_host = x_pin.numpy()
-    e2e_s = []
-    for i in range(args.warmup + args.steps):
+    e2e_s, ok_e2e = [], 0
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
         t0 = time.perf_counter()
         rh = H.value(sysd, x_host, w["t"], opts)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             e2e_s.append(dt)
-    ok_e2e = int((rh["status"] == 0).sum())
+            ok_e2e = int((rh["status"] == 0).sum())
+    if not e2e_s:
+        e2e_s = [float("nan")]
 
     mean_ms = statistics.mean(step_ms)
+    POINTS_ = points
     t_local = np.array([mean_ms, statistics.mean(e2e_s) * 1e3], dtype=np.float64)
     if dist:
         tt = torch.tensor(t_local, device="cuda")
@@ -249,19 +275,22 @@ def main():
     sms = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x max SM clock
-    h2d = POINTS * n * 4 + 4
-    d2h = POINTS * (4 + 4 * n + 4 + 4 + 4)
+    h2d = POINTS_ * n * 4 + 4
+    d2h = POINTS_ * (4 + 4 * n + 4 + 4 + 4)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(t_local[0]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; random n=10 system, x~N(0,4I))",
-        "config": {"workload": "random_n10_m2_t2_N256_65536pts", "n": n, "m": m, "N": N, "t": w["t"],
-                   "points_per_gpu": POINTS, "tol_gap": TOL, "tau": w["tau"], "start": "cold",
+        "config": {"workload": f"random_n10_m2_t2_N256_{POINTS_}pts", "n": n, "m": m, "N": N, "t": w["t"],
+                   "points_per_gpu": POINTS_, "tol_gap": TOL, "tau0": TAU_ACCEL,
+                   "start": "cold", "iteration": "accelerated (strongly convex G)",
                    "l2": "flushed between timed steps (512 MB write)",
-                   "mean_iters": units / args.steps / POINTS - 1.0,
+                   "mean_iters": float(iters_last.mean()), "p99_iters": float(np.percentile(iters_last, 99)),
+                   "max_iters": int(iters_last.max()),
                    "certified_per_step": solves_per_step,
-                   "ms_tables": statistics.mean(table_ms), "ms_solve": statistics.mean(solve_ms)},
+                   "ms_tables": statistics.mean(table_ms), "ms_solve": statistics.mean(solve_ms),
+                   "plain_cold_eq15": plain},
         "roofline": {"bound": "alu", "kernel": "pdhg_small_kernel<10,2,4>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",

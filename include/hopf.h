@@ -97,11 +97,22 @@ typedef struct {
     int profile;        /* non-zero: record CUDA events around the table build
                            and the solve kernel of hopf_value (see
                            hopf_last_profile)                                     */
+    int accel;          /* 0: the iteration of Eq. 15 with theta = 1 (§VI).
+                           1: the accelerated variant for a strongly convex G
+                           that §III names (Chambolle and Pock 2011, Alg. 2):
+                           G of Eq. 36 is gamma-strongly convex with
+                           gamma = lambda_min(M)/2; after each step
+                           theta = 1/sqrt(1 + 2 gamma tau), tau *= theta,
+                           sigma /= theta, pbar = p + theta (p - p_old).  The
+                           starting tau is opts->tau.                             */
 } hopf_opts;
 
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,
  * gap_every 8, FP32, device io, tau 1, sigma_scale 1 (§VI: sigma = 1/(tau |K|^2)),
- * tol_gap 1e-5, t_max 10, tol_T 1e-5. */
+ * tol_gap 1e-5, t_max 10, tol_T 1e-5, no profiling, accel 0.
+ * A point counts as converged when its computed relative gap plus an
+ * allowance for the rounding of P and D (4 u (|P parts| + |D| + 1) / scale,
+ * u the unit roundoff of the iteration's precision) is <= tol_gap. */
 void hopf_default_opts(hopf_opts *opts);
 
 /*

@@ -14,6 +14,8 @@ Control and Trajectory Generation in High-Dimensional Systems"):
   * node matrices K_i ....................... §III.A, Eq. 16 and Eq. 20
   * quadratic terminal cost and its conjugate §VI.A, Eq. 34 - Eq. 37
   * primal-dual iteration ................... §III, Eq. 15 with Eq. 22, Eq. 23, Eq. 37
+  * accelerated iteration for a strongly convex G (named in §III, from
+    Chambolle and Pock 2011, Algorithm 2) ..... pdhg(..., accel=True)
   * duality gap (stopping rule) ............. §III.B (primal/dual residuals) and
                                               the Fenchel dual of Eq. 18
   * time-to-reach ........................... §IV (zero of phi(x, T) in T, bisection)
@@ -201,7 +203,7 @@ def relative_gap(Pv, Dv):
 
 
 # ---------------------------------------------------------------------- PDHG
-def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None):
+def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel=False):
     """Chambolle-Pock iteration of Eq. 15 for every point in x0 (P, n).
 
       y <- prox_{sigma F*}(y + sigma K pbar)   (Eq. 23: projection onto w_i U per node)
@@ -211,6 +213,13 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None):
     Initial point of §VI: p0 = pbar0 = x0, y0 = K p0 (unless given).
     A point stops at the first iteration whose relative gap is <= tol, or whose
     ``stop(P, D)`` predicate holds; its iterate is then frozen.
+
+    accel=True is the variant for a strongly convex G that §III mentions
+    (Chambolle and Pock 2011, Algorithm 2): G of Eq. 36 has Hessian M/2, so it
+    is gamma-strongly convex with gamma = lambda_min(M)/2; after each step
+    theta = 1/sqrt(1 + 2 gamma tau), tau <- theta tau, sigma <- sigma/theta and
+    pbar = p_new + theta (p_new - p).  The prox of G is then (I + tau M/2)^-1
+    at the current tau, evaluated by a fresh linear solve.
     Returns dict(phi=-P, p, y, P, D, gap, iters, status)."""
     x0 = np.atleast_2d(np.asarray(x0, dtype=np.float64))
     P_, n = x0.shape
@@ -226,6 +235,12 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None):
     Pv = np.full(P_, np.inf)
     Dv = np.full(P_, -np.inf)
     active = np.arange(P_)
+    tau_k = np.full(P_, float(tau))
+    sig_k = np.array(sigma, dtype=np.float64)
+    if accel:
+        Mb = pb["M"] if pb["M"].shape[0] == P_ else np.broadcast_to(pb["M"], (P_,) + pb["M"].shape[1:])
+        gamma = 0.5 * np.linalg.eigvalsh(Mb)[:, 0]
+        eye = np.eye(n)
 
     def sub(a, idx):
         return a if shared else a[idx]
@@ -234,14 +249,23 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None):
         if active.size == 0:
             break
         Ka, wa, Sa = sub(K, active), sub(w, active), sub(S, active)
-        sa = sigma[active]
+        sa = sig_k[active]
+        ta = tau_k[active]
         # dual step: projection of y_i + sigma K_i pbar onto w_i U (Eq. 23)
         v = y[active] + sa[:, None, None] * _Kp(Ka, pbar[active])
         ynew = project_scaled(kind, v, np.broadcast_to(wa, v.shape[:-1]))
         # primal step: prox of G (Eq. 37)
-        rhs = p[active] - tau * _KTy(Ka, ynew) + tau * x0[active]
-        pnew = np.einsum("...ij,...j->...i", Sa, rhs)
-        pbar[active] = 2.0 * pnew - p[active]
+        rhs = p[active] - ta[:, None] * _KTy(Ka, ynew) + ta[:, None] * x0[active]
+        if accel:
+            A_ = eye + 0.5 * ta[:, None, None] * np.broadcast_to(sub(pb["M"], active), (active.size, n, n))
+            pnew = np.linalg.solve(A_, rhs[..., None])[..., 0]
+            th = 1.0 / np.sqrt(1.0 + 2.0 * gamma[active] * ta)
+            tau_k[active] = th * ta
+            sig_k[active] = sa / th
+            pbar[active] = pnew + th[:, None] * (pnew - p[active])
+        else:
+            pnew = np.einsum("...ij,...j->...i", Sa, rhs)
+            pbar[active] = 2.0 * pnew - p[active]
         p[active] = pnew
         y[active] = ynew
         iters[active] = k
@@ -268,7 +292,7 @@ def terminal_cost(sysd, x):
     return np.einsum("...i,ij,...j->...", x, Wi, x) - 1.0
 
 
-def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_scale=1.0):
+def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_scale=1.0, accel=False):
     """phi_N(x, T): the generalized Hopf formula with the N-node quadrature
     (Eq. 18) for every row of x at one horizon T.  At T = 0 the value is the
     terminal cost itself (Eq. 4 initial condition) and p* = grad J_x."""
@@ -280,7 +304,7 @@ def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_sc
                     iters=np.zeros(P_, dtype=np.int64), status=np.zeros(P_, dtype=np.int64),
                     P=-terminal_cost(sysd, x), D=-terminal_cost(sysd, x))
     prob = setup(sysd, T, N, rule, tau, sigma_scale)
-    return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0)
+    return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0, accel=accel)
 
 
 # ---------------------------------------------------------------- time-to-reach

@@ -18,7 +18,8 @@ class HopfProblem(ctypes.Structure):
 class HopfOpts(ctypes.Structure):
     _fields_ = [("rule", c_int), ("N", c_int), ("max_iter", c_int), ("gap_every", c_int),
                 ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
-                ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int)]
+                ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int),
+                ("accel", c_int)]
 
 
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",

@@ -63,11 +63,12 @@ class Options:
     t_max: float = 10.0
     tol_T: float = 1e-5
     profile: bool = False
+    accel: bool = False
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
-                             int(self.profile))
+                             int(self.profile), int(self.accel))
 
 
 def _is_torch(a):

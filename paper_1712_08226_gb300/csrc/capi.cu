@@ -175,6 +175,7 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
         if (!(o->tau > 0.0) || !(o->sigma_scale > 0.0) || !(o->sigma_scale <= 1.0))
             return fail(HOPF_EINVAL, "need tau > 0 and 0 < sigma_scale <= 1");
         if (!(o->tol_gap >= 0.0)) return fail(HOPF_EINVAL, "bad tol_gap");
+        if (o->accel != 0 && o->accel != 1) return fail(HOPF_EINVAL, "accel must be 0 or 1");
     }
     return HOPF_SUCCESS;
 }
@@ -241,8 +242,8 @@ SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
     int pad = 0;
     while ((((N + pad) * m) % 32) != ((SMALL_TPP * m) % 32)) ++pad;
     sp.ys_stride = (N + pad) * m;
-    const size_t fixed = sizeof(float) * ((size_t)N * KR + 3 * sp.NS * sp.NS);
-    const size_t per_pt = sizeof(float) * (size_t)sp.ys_stride;
+    const size_t fixed = sizeof(float) * ((size_t)N * KR + 4 * sp.NS * sp.NS + ((sp.NS + 3) & ~3));
+    const size_t per_pt = sizeof(float) * ((size_t)sp.ys_stride + sp.NS);
     const size_t budget = dev.smem_optin;
     if (fixed + 8 * per_pt > budget) return sp;
     int pts = (int)((budget - fixed) / per_pt);
@@ -269,6 +270,7 @@ void fill_params(SolveParams &prm, const hopf_problem *pr, const hopf_opts *o, i
     prm.warm = 0;
     prm.sign_mode = 0;
     prm.inst_stride = 0;
+    prm.accel = o->accel;
     prm.tau = o->tau;
     prm.tol_gap = o->tol_gap;
     prm.sign_floor = o->precision == HOPF_FP64 ? 1e-13 : 1e-6;

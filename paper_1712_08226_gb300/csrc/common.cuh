@@ -7,7 +7,9 @@
 //   M    [n][n]     V(0)^-1 = e^{-TA} W e^{-TA^T}               (§VI.A, Eq. 35)
 //   V    [n][n]     M^-1
 //   S    [n][n]     (I + tau M / 2)^-1                          (Eq. 37)
-//   sc   [4]        sigma, T, |K|^2, flag (1 = T == 0)
+//   U    [n][n]     eigenvectors of M (M = U diag(lam) U^T), for the
+//   lam  [n]        accelerated iteration whose step tau changes every step
+//   sc   [8]        sigma, T, |K|^2, flag (1 = T == 0), gamma = lambda_min(M)/2
 // A float32 copy with the same layout is made for the float32 kernels.
 #pragma once
 #include <cuda_runtime.h>
@@ -19,7 +21,7 @@ namespace hopf {
 
 struct InstanceLayout {
     // element offsets (in elements of the instance's type) inside one instance
-    long long K, w, M, V, S, sc, stride;
+    long long K, w, M, V, S, U, lam, sc, stride;
     __host__ __device__ static InstanceLayout make(int n, int m, int N) {
         InstanceLayout L;
         long long o = 0;
@@ -29,7 +31,9 @@ struct InstanceLayout {
         L.M = o;  o = al(o + (long long)n * n);
         L.V = o;  o = al(o + (long long)n * n);
         L.S = o;  o = al(o + (long long)n * n);
-        L.sc = o; o = al(o + 4);
+        L.U = o;  o = al(o + (long long)n * n);
+        L.lam = o; o = al(o + n);
+        L.sc = o; o = al(o + 8);
         L.stride = o;
         return L;
     }
@@ -43,6 +47,7 @@ struct SolveParams {
     int warm;          // p_init given
     int sign_mode;     // time-to-reach: stop once the sign of phi is certified
     int inst_stride;   // 0: one shared instance, 1: instance k for point k
+    int accel;         // Chambolle-Pock accelerated variant (strongly convex G)
     double tau, tol_gap, sign_floor;
 };
 
@@ -51,7 +56,19 @@ __host__ __device__ inline long long table_scratch_doubles(int n, int m) {
     return 9LL * n * n + 2LL * n * m + 2LL * n + 16;
 }
 
-enum { SC_SIGMA = 0, SC_T = 1, SC_L2 = 2, SC_ZERO = 3 };
+enum { SC_SIGMA = 0, SC_T = 1, SC_L2 = 2, SC_ZERO = 3, SC_GAMMA = 4 };
+
+// unit roundoff of the iteration's arithmetic
+template <typename R> struct Unit;
+template <> struct Unit<float> { static constexpr double u = 5.9604644775390625e-08; };
+template <> struct Unit<double> { static constexpr double u = 1.1102230246251565e-16; };
+
+// Float rounding allowance added to the computed relative gap before it is
+// compared with the tolerance: 4 u times the magnitude of the terms of P and D.
+template <typename R>
+__device__ __forceinline__ R gap_allowance(R quad, R H, R Dv, R scale) {
+    return R(4.0 * Unit<R>::u) * (fabs(quad) + H + fabs(Dv) + R(1)) / scale;
+}
 
 // Relative duality gap (P - D) / max(1, |P|, |D|).
 template <typename R>

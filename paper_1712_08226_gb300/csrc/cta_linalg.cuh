@@ -176,5 +176,76 @@ __device__ inline double lambda_max(const double *C, int n, double *v, double *u
     return lam;
 }
 
+// Eigen-decomposition of a symmetric matrix by cyclic Jacobi rotations
+// (Jacobi 1846; each rotation in the (p, q) plane annihilates a_pq:
+// theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
+// c = 1/sqrt(t^2 + 1), s = t c).  A (n x n, destroyed) becomes diagonal;
+// U (n x n) collects the rotations so that A_in = U diag(lam) U^T.
+__device__ inline void sym_eig(double *A, double *U, double *lam, int n, double *red) {
+    set_identity(U, n);
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (threadIdx.x == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    double v = A[i * n + j] * A[i * n + j];
+                    tot += v;
+                    if (i != j) off += v;
+                }
+            red[0] = off;
+            red[1] = tot;
+        }
+        __syncthreads();
+        bool done = !(red[0] > 1e-30 * red[1]);
+        __syncthreads();
+        if (done) break;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                if (threadIdx.x == 0) {
+                    double apq = A[p * n + q];
+                    double c = 1.0, s = 0.0, t = 0.0;
+                    if (apq != 0.0) {
+                        double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                        t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                    red[2] = c;
+                    red[3] = s;
+                    red[4] = t;
+                    red[5] = apq;
+                }
+                __syncthreads();
+                const double c = red[2], s = red[3], t = red[4], apq = red[5];
+                if (apq != 0.0) {
+                    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                        if (k != p && k != q) {
+                            double akp = A[k * n + p], akq = A[k * n + q];
+                            double np_ = c * akp - s * akq, nq_ = s * akp + c * akq;
+                            A[k * n + p] = np_;
+                            A[p * n + k] = np_;
+                            A[k * n + q] = nq_;
+                            A[q * n + k] = nq_;
+                        }
+                        double ukp = U[k * n + p], ukq = U[k * n + q];
+                        U[k * n + p] = c * ukp - s * ukq;
+                        U[k * n + q] = s * ukp + c * ukq;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        A[p * n + p] -= t * apq;
+                        A[q * n + q] += t * apq;
+                        A[p * n + q] = 0.0;
+                        A[q * n + p] = 0.0;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[i * n + i];
+    __syncthreads();
+}
+
 }  // namespace cta
 }  // namespace hopf

@@ -54,9 +54,11 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     const R *I = inst_base + (prm.inst_stride ? (long long)k * L.stride : 0LL);
     const R *K = I + L.K, *w = I + L.w, *M = I + L.M, *V = I + L.V, *S = I + L.S, *sc = I + L.sc;
-    const R sigma = sc[SC_SIGMA];
+    R sigma = sc[SC_SIGMA];
+    const R gamma = sc[SC_GAMMA];
     const bool zero = sc[SC_ZERO] != R(0);
-    const R tau = (R)prm.tau;
+    R tau = (R)prm.tau;
+    const R *U = I + L.U, *lam = I + L.lam;
     R *y = y_scratch + (long long)k * N * m;
     const bool ball = prm.ctrl_kind == HOPF_BALL;
 
@@ -154,11 +156,13 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
                 for (int l = 0; l < n; ++l) s = fma(M[j * n + l], pb[l], s);
                 part += pb[j] * (R(0.25) * s - x0[j]);
             }
-            Pc = warp_sum(part) + R(1) + H;
+            const R quad = warp_sum(part) + R(1);
+            Pc = quad + H;
             Dc = Dprev;
             gc = rel_gap(Pc, Dc);
             if (!isfinite(Pc) || !isfinite(Dc)) { st = HOPF_NONFINITE; break; }
-            bool conv = gc <= (R)prm.tol_gap;
+            const R scl = fmax(R(1), fmax(fabs(Pc), fabs(Dc)));
+            bool conv = gc + gap_allowance(quad, H, Dc, scl) <= (R)prm.tol_gap;
             if (prm.sign_mode) conv = conv || Pc < R(0) || Dc > R(0) || gc <= (R)prm.sign_floor;
             if (conv) { st = HOPF_OK; break; }
             if (it > prm.max_iter) { st = HOPF_MAXITER; break; }
@@ -176,11 +180,30 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
             vt[j] = p[j] - tau * s + tau * x0[j];
         }
         __syncwarp();
-        for (int j = lane; j < n; j += 32) {
-            R s = 0;
-            for (int l = 0; l < n; ++l) s = fma(S[j * n + l], vt[l], s);
-            pb[j] = R(2) * s - p[j];
-            p[j] = s;
+        if (prm.accel) {
+            // prox of G at the current tau: U diag(1 / (1 + tau lam / 2)) U^T vt
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(U[l * n + j], vt[l], s);
+                qv[j] = s / fma(R(0.5) * tau, lam[j], R(1));
+            }
+            __syncwarp();
+            const R th = R(1) / sqrt(fma(R(2) * gamma, tau, R(1)));
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(U[j * n + l], qv[l], s);
+                pb[j] = fma(th, s - p[j], s);
+                p[j] = s;
+            }
+            tau *= th;
+            sigma /= th;
+        } else {
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(S[j * n + l], vt[l], s);
+                pb[j] = R(2) * s - p[j];
+                p[j] = s;
+            }
         }
         __syncwarp();
         if (is_check(it + 1)) {

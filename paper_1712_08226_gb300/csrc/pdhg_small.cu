@@ -97,7 +97,10 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
     float *Ss = Ks + (size_t)N * KR;
     float *Msm = Ss + NS * NS;
     float *Vs = Msm + NS * NS;
-    float *Ys = Vs + NS * NS;
+    float *Us = Vs + NS * NS;
+    float *lams = Us + NS * NS;
+    float *X0s = lams + ((NS + 3) & ~3);          // [slots][NS] query points
+    float *Ys = X0s + (size_t)(blockDim.x / TPP) * NS;
 
     // stage the table once per block, zero-padding the state to NS components
     for (int e = threadIdx.x; e < N * KR; e += blockDim.x) {
@@ -117,12 +120,16 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
         Ss[e] = in ? inst[L.S + a * n + b] : (a == b ? 1.f : 0.f);
         Msm[e] = in ? inst[L.M + a * n + b] : 0.f;
         Vs[e] = in ? inst[L.V + a * n + b] : 0.f;
+        Us[e] = in ? inst[L.U + a * n + b] : (a == b ? 1.f : 0.f);
     }
+    for (int e = threadIdx.x; e < NS; e += blockDim.x) lams[e] = e < n ? inst[L.lam + e] : 0.f;
     __syncthreads();
 
-    const float sigma = inst[L.sc + SC_SIGMA];
+    const float sigma0 = inst[L.sc + SC_SIGMA];
+    const float gamma = inst[L.sc + SC_GAMMA];
+    const bool accel = prm.accel != 0;
     const bool zero = inst[L.sc + SC_ZERO] != 0.f;
-    const float tau = (float)prm.tau;
+    const float tau0 = (float)prm.tau;
     const float tol = (float)prm.tol_gap;
     const bool ball = prm.ctrl_kind == HOPF_BALL;
     const int g = prm.gap_every;
@@ -133,11 +140,13 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
     const int lead = lane - q;
     const unsigned gmask = (TPP == 32) ? 0xffffffffu : (((1u << TPP) - 1u) << lead);
     float *ys = Ys + (size_t)slot * ys_stride;
+    float *x0 = X0s + (size_t)slot * NS;
 
-    float p[NS], pb[NS], acc[NS], x0[NS];
+    float p[NS], pb[NS], acc[NS];
     int pt = -1, it_pt = 0;
     bool idle = false, have_D = false, fresh = false;
     float Dprev = 0.f;
+    float tau = tau0, sigma = sigma0;      // current steps (they change only when accelerated)
 
     // take the next point for this group; T = 0 points finish on the spot
     auto fetch = [&]() {
@@ -147,8 +156,12 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             nx = __shfl_sync(gmask, nx, lead);
             if (nx >= P) { idle = true; pt = -1; return; }
             pt = nx;
+            __syncwarp(gmask);
+            if (q == 0) {
 #pragma unroll
-            for (int j = 0; j < NS; ++j) x0[j] = (j < n) ? x[(size_t)pt * n + j] : 0.f;
+                for (int j = 0; j < NS; ++j) x0[j] = (j < n) ? x[(size_t)pt * n + j] : 0.f;
+            }
+            __syncwarp(gmask);
             if (!zero) break;
             float J = -1.f;
 #pragma unroll
@@ -197,6 +210,8 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
         it_pt = 0;
         have_D = false;
         fresh = true;
+        tau = tau0;
+        sigma = sigma0;
     };
 
     fetch();
@@ -231,7 +246,8 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                 const float Dc = Dprev;
                 const float gc = rel_gap(Pc, Dc);
                 const bool bad = !isfinite(Pc) || !isfinite(Dc);
-                const bool conv = gc <= tol;
+                const float scl = fmaxf(1.f, fmaxf(fabsf(Pc), fabsf(Dc)));
+                const bool conv = gc + gap_allowance(quad, hs, Dc, scl) <= tol;
                 if (bad || conv || it_pt - 1 >= prm.max_iter) {
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
@@ -251,16 +267,39 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             float pn[NS], v[NS];
 #pragma unroll
             for (int b = 0; b < NS; ++b) v[b] = fmaf(-tau, acc[b], fmaf(tau, x0[b], p[b]));
+            float th = 1.f;
+            if (accel) {
+                // (I + tau M/2)^-1 v = U diag(1 / (1 + tau lam / 2)) U^T v
+                float z[NS];
 #pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                float s = 0.f;
+                for (int a = 0; a < NS; ++a) {
+                    float s = 0.f;
 #pragma unroll
-                for (int b = 0; b < NS; ++b) s = fmaf(Ss[a * NS + b], v[b], s);
-                pn[a] = s;
+                    for (int b = 0; b < NS; ++b) s = fmaf(Us[b * NS + a], v[b], s);
+                    z[a] = __fdividef(s, fmaf(0.5f * tau, lams[a], 1.f));
+                }
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) s = fmaf(Us[a * NS + b], z[b], s);
+                    pn[a] = s;
+                }
+                th = rsqrtf(fmaf(2.f * gamma, tau, 1.f));
+                tau *= th;
+                sigma /= th;
+            } else {
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) s = fmaf(Ss[a * NS + b], v[b], s);
+                    pn[a] = s;
+                }
             }
 #pragma unroll
             for (int j = 0; j < NS; ++j) {
-                pb[j] = 2.f * pn[j] - p[j];
+                pb[j] = fmaf(th, pn[j] - p[j], pn[j]);
                 p[j] = pn[j];
             }
             if (((wit + 1) % g) == 0) {

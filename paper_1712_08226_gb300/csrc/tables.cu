@@ -92,12 +92,18 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
             So[e] = okS ? T2[e] : __longlong_as_double(0x7ff8000000000000LL);
         __syncthreads();
         double L2 = cta::lambda_max(C, n, v, u, red);
+        // M = U diag(lam) U^T for the accelerated prox (I + tau M/2)^-1 = U diag(1/(1 + tau lam/2)) U^T
+        cta::copy(T2, Mo, n * n);
+        cta::sym_eig(T2, o + L.U, o + L.lam, n, red);
         if (threadIdx.x == 0) {
+            double lmin = o[L.lam];
+            for (int i = 1; i < n; ++i) lmin = fmin(lmin, o[L.lam + i]);
             double *s = o + L.sc;
             s[SC_SIGMA] = (L2 > 0.0) ? sigma_scale / (tau * L2) : 0.0;
             s[SC_T] = T;
             s[SC_L2] = L2;
             s[SC_ZERO] = (T == 0.0) ? 1.0 : 0.0;
+            s[SC_GAMMA] = fmax(0.5 * lmin, 0.0);
         }
         __syncthreads();
         if (out32) {

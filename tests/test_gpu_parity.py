@@ -247,3 +247,32 @@ def test_trajectory_matches_oracle_fp64(H):
         assert np.linalg.norm(xt[k, -1] - xs[-1]) <= 1e-4
         assert np.max(np.abs(xt[k] - xs)) <= 1e-6
         assert np.allclose(np_(r["u"])[k], us)
+
+
+# ------------------------------------------------- accelerated iteration
+@pytest.mark.parametrize("per_point_t", [False, True])
+def test_random10_accelerated_fp32(H, per_point_t):
+    g = gold("random10_values.json")
+    P = 320 if not per_point_t else 64
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], tau=2.0, tol_gap=1e-5, precision=H.FP32, accel=True)
+    t = cuda(np.full(P, w["t"])) if per_point_t else w["t"]
+    r = H.value(sysd, cuda(w["x"]), t, opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"][:P]))
+    assert err.max() <= 1e-5, err.max()
+
+
+def test_di_accelerated_fp64(H):
+    import torch
+    g = gold("di_values_T1.5.json")
+    w = wl.workload_di(g["meta"]["P"])
+    sysd = H.System.from_dict(w["system"])
+    # the accelerated steps shrink tau like 1/k, so very tight gaps are slow to
+    # reach; 1e-8 is still far below the float32 tolerance
+    opts = H.Options(N=w["N"], rule=H.TRAPEZOID, tau=w["tau"], tol_gap=1e-8, precision=H.FP64,
+                     max_iter=1000000, accel=True)
+    r = H.value(sysd, cuda(w["x"], torch.float64), g["meta"]["T"], opts)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    assert rel_err(np_(r["phi"]), np.array(g["phi"])).max() <= 1e-8

@@ -247,3 +247,20 @@ def test_di_control_sign_matches_switching_curve():
         u0 = oh.optimal_control(sysd, tt["p"][0], 1e-3)
         sw = x0[0] + 0.5 * x0[1] * abs(x0[1])
         assert np.sign(u0[0]) == -np.sign(sw)
+
+
+def test_accelerated_iteration_reaches_the_same_value():
+    # Chambolle-Pock Algorithm 2 (strongly convex G, §III) converges to the same
+    # discretised value; pinned against the independent projected-gradient solver.
+    sysd = wl.random_system(11, 4, 2)
+    x = wl.normal_points(12, 3, 4, 1.0)
+    res = oh.value(sysd, x, 0.8, 24, oh.LEFT_RIEMANN, tau=2.0, tol=1e-12, accel=True)
+    assert np.all(res["status"] == oh.OK)
+    for k in range(3):
+        ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x[k], 0.8, 24, "ball")
+        assert abs(res["phi"][k] - ref) <= 1e-8 * max(1.0, abs(ref))
+    sysd = wl.double_integrator(0.1)
+    x0 = np.array([0.6, -0.3])
+    r1 = oh.value(sysd, x0, 1.0, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, accel=True)
+    ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 32, "box", trapezoid=True)
+    assert abs(r1["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
