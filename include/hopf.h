@@ -70,6 +70,8 @@ extern "C" {
 #define HOPF_ECUDA (-3)        /* a CUDA runtime call failed                    */
 #define HOPF_ENOMEM (-4)       /* device allocation failed                      */
 #define HOPF_ENONFINITE (-5)   /* non-finite A, B, W or bounds                  */
+#define HOPF_ESCRATCH (-6)     /* hopf_value_noalloc: the call does not fit the
+                                  library's static scratch array               */
 
 typedef struct {
     int n;                      /* state dimension, >= 1                         */
@@ -184,6 +186,45 @@ int hopf_release_workspace(void);
  * milliseconds, measured with CUDA events on the call's stream.  Waits for
  * the call to finish.  Returns HOPF_EINVAL if no profiled call was made. */
 int hopf_last_profile(double *ms_tables, double *ms_solve);
+
+/*
+ * hopf_value_noalloc - hopf_value for callers that cannot allocate memory.
+ *
+ * The paper has no counterpart; this is a deployment variant.  Some callers
+ * must not allocate at solve time: a hard real-time control loop (a device
+ * allocation can synchronise the whole device and has no time bound), code
+ * that runs while a CUDA graph is being captured (allocation calls are not
+ * allowed there), or a process whose memory footprint is fixed after start-up.
+ * This entry point takes all of its scratch (a copy of A, B, Q and W, the node
+ * tables, and each point's dual variable) from one static device array of
+ * HOPF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits, and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  It always runs the general warp-per-point kernel.
+ *
+ * Arguments and results are those of hopf_value, with these limits:
+ *   - opts->host_io must be 0 (x, t, p_init and outputs are device arrays);
+ *   - n <= HOPF_NOALLOC_MAX_N, m <= 16;
+ *   - the scratch the call needs must fit the array, about
+ *     8 (n_tables (N m n + N + 4 n^2 + n) + 9 n^2) + P N m sizeof(element)
+ *     bytes with n_tables = 1 (t_stride 0) or P (t_stride 1); otherwise the
+ *     call returns HOPF_ESCRATCH and does nothing.
+ *   Validation failures return the codes of hopf_value; hopf_last_error() is
+ *   not updated by this entry point.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current and keeps it; make that first call before any stream
+ * capture.  Every call shares the one array and it keeps the last call's
+ * contents (no part of it needs to start at zero: a call writes every scratch
+ * byte before reading it).  Calls that overlap on the GPU - on different
+ * streams, or from host threads without ordering between them - race on the
+ * array and give wrong results; calls ordered on one stream are safe.
+ */
+#define HOPF_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
+#define HOPF_NOALLOC_MAX_N 64
+int hopf_value_noalloc(const hopf_problem *prob, const hopf_opts *opts, int P,
+                       const void *x, const void *t, int t_stride, const void *p_init,
+                       void *phi, void *p_star, void *gap, int *iters, int *status,
+                       void *stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ class HopfOpts(ctypes.Structure):
 
 
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",
-           "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile")
+           "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile",
+           "hopf_value_noalloc")
 
 _lib = None
 
@@ -57,5 +58,7 @@ def load(path=LIB_PATH):
     lib.hopf_release_workspace.restype = c_int
     lib.hopf_last_profile.argtypes = [P_double, P_double]
     lib.hopf_last_profile.restype = c_int
+    lib.hopf_value_noalloc.argtypes = lib.hopf_value.argtypes
+    lib.hopf_value_noalloc.restype = c_int
     _lib = lib
     return lib

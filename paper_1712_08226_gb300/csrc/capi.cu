@@ -651,6 +651,7 @@ const char *hopf_status_string(int code) {
         case HOPF_ECUDA: return "CUDA error";
         case HOPF_ENOMEM: return "device allocation failed";
         case HOPF_ENONFINITE: return "non-finite problem data";
+        case HOPF_ESCRATCH: return "does not fit the static scratch of hopf_value_noalloc";
         default: return "unknown";
     }
 }
