@@ -187,6 +187,62 @@ int hopf_release_workspace(void);
  * the call to finish.  Returns HOPF_EINVAL if no profiled call was made. */
 int hopf_last_profile(double *ms_tables, double *ms_solve);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start.  The paper has no learned part; these entry points
+ * serve the warm-started batched solve: a small network predicts p* from x,
+ * the primal-dual iteration starts from the prediction, and any point whose
+ * warm solve is not certified is solved again from the cold start of §VI.
+ *
+ * Network: n_in -> hidden -> hidden -> n_out, exact GELU after each hidden
+ * layer, inputs standardised by (x - x_shift)/x_scale, outputs mapped back by
+ * out * y_scale + y_shift.  Weights are used as bfloat16, all products
+ * accumulate in float32; a float32 master copy is kept for training.
+ * Parameter layout (both copies): W1[hidden][n_in], b1[hidden],
+ * W2[hidden][hidden], b2[hidden], W3[n_out][hidden], b3[n_out], row-major.
+ * All pointers are caller-owned device arrays.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int n_in, hidden, n_out;
+    float *w;                 /* float32 master parameters, hopf_mlp_param_count() */
+    void *w_bf16;             /* bfloat16 copy used by the products, same count    */
+    float *adam_m, *adam_v;   /* optimiser moments (training only; may be NULL)     */
+    const float *x_shift, *x_scale;   /* [n_in]  */
+    const float *y_shift, *y_scale;   /* [n_out] */
+} hopf_mlp;
+
+/* Number of parameters of the network (weights and biases). */
+long long hopf_mlp_param_count(int n_in, int hidden, int n_out);
+
+/* Refreshes the bfloat16 copy from the float32 master parameters. */
+int hopf_mlp_sync(const hopf_mlp *net, void *stream);
+
+/* y[B][n_out] = prediction for x[B][n_in] (physical units). */
+int hopf_mlp_forward(const hopf_mlp *net, int B, const float *x, float *y, void *stream);
+
+/* Mean squared error of the standardised output against the standardised
+ * target y[B][n_out], written to *loss (device float), and its gradient with
+ * respect to every parameter (grad: param_count floats, device). */
+int hopf_mlp_loss_grad(const hopf_mlp *net, int B, const float *x, const float *y, float *loss,
+                       float *grad, void *stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the master parameters with
+ * gradient grad; refreshes the bfloat16 copy. */
+int hopf_mlp_adam(const hopf_mlp *net, const float *grad, int step, double lr, double beta1,
+                  double beta2, double eps, void *stream);
+
+/*
+ * hopf_value_warm - hopf_value (float32 only) with the network's prediction
+ * as the warm start p_init.  Each warm solve runs at most max_iter_warm
+ * iterations; a point that is not certified (status != HOPF_OK) is solved
+ * again from the cold start with opts->max_iter, and its outputs are those of
+ * the cold solve.  Outputs as in hopf_value.  n_fallback: NULL or a device
+ * int that receives the number of points solved again.
+ */
+int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_mlp *net, int P,
+                    const void *x, const void *t, int t_stride, int max_iter_warm,
+                    void *phi, void *p_star, void *gap, int *iters, int *status,
+                    int *n_fallback, void *stream);
+
 /*
  * hopf_value_noalloc - hopf_value for callers that cannot allocate memory.
  *

@@ -22,9 +22,16 @@ class HopfOpts(ctypes.Structure):
                 ("accel", c_int)]
 
 
+class HopfMlp(ctypes.Structure):
+    _fields_ = [("n_in", c_int), ("hidden", c_int), ("n_out", c_int), ("w", c_void_p), ("w_bf16", c_void_p),
+                ("adam_m", c_void_p), ("adam_v", c_void_p), ("x_shift", c_void_p), ("x_scale", c_void_p),
+                ("y_shift", c_void_p), ("y_scale", c_void_p)]
+
+
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",
            "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile",
-           "hopf_value_noalloc")
+           "hopf_value_noalloc", "hopf_mlp_param_count", "hopf_mlp_sync", "hopf_mlp_forward",
+           "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm")
 
 _lib = None
 
@@ -60,5 +67,19 @@ def load(path=LIB_PATH):
     lib.hopf_last_profile.restype = c_int
     lib.hopf_value_noalloc.argtypes = lib.hopf_value.argtypes
     lib.hopf_value_noalloc.restype = c_int
+    PM = ctypes.POINTER(HopfMlp)
+    lib.hopf_mlp_param_count.argtypes = [c_int, c_int, c_int]
+    lib.hopf_mlp_param_count.restype = ctypes.c_longlong
+    lib.hopf_mlp_sync.argtypes = [PM, c_void_p]
+    lib.hopf_mlp_sync.restype = c_int
+    lib.hopf_mlp_forward.argtypes = [PM, c_int, c_void_p, c_void_p, c_void_p]
+    lib.hopf_mlp_forward.restype = c_int
+    lib.hopf_mlp_loss_grad.argtypes = [PM, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hopf_mlp_loss_grad.restype = c_int
+    lib.hopf_mlp_adam.argtypes = [PM, c_void_p, c_int, c_double, c_double, c_double, c_double, c_void_p]
+    lib.hopf_mlp_adam.restype = c_int
+    lib.hopf_value_warm.argtypes = [PP, PO, PM, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hopf_value_warm.restype = c_int
     _lib = lib
     return lib

@@ -1,4 +1,5 @@
 // C ABI entry points (include/hopf.h): argument checks, workspace, launches.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +45,23 @@ template <typename R>
 cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                               const double *qd, int n, int m, int ctrl_kind, int P, const R *x, const R *T,
                               const R *pstar, int S, R *xt, R *ut, double *scratch);
+long long mlp_param_count(int n_in, int h, int n_out);
+long long mlp_scratch_floats(int n_in, int h, int n_out, int B, bool train);
+cudaError_t mlp_forward(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,
+                        const float *x_scale, const float *y_shift, const float *y_scale, int B, const float *x,
+                        float *y, float *scratch, bool keep_pre, cudaStream_t s);
+cudaError_t mlp_loss_grad(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,
+                          const float *x_scale, const float *y_shift, const float *y_scale, int B, const float *x,
+                          const float *y, float *loss, float *grad, float *scratch, cudaStream_t s);
+cudaError_t mlp_adam(long long count, float *w, __nv_bfloat16 *wb, const float *g, float *m, float *v, float lr,
+                     float b1, float b2, float eps, int step, cudaStream_t s);
+cudaError_t mlp_sync_bf16(long long count, const float *w, __nv_bfloat16 *wb, cudaStream_t s);
+
+// list of the points whose status is not OK (order unspecified)
+__global__ void failed_points_kernel(int P, const int *status, int *list, int *count) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P && status[k] != HOPF_OK) list[atomicAdd(count, 1)] = k;
+}
 }  // namespace hopf
 
 using namespace hopf;
@@ -260,6 +278,7 @@ SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
 }
 
 void fill_params(SolveParams &prm, const hopf_problem *pr, const hopf_opts *o, int P) {
+    prm = SolveParams{};
     prm.n = pr->n;
     prm.m = pr->m;
     prm.N = o->N;
@@ -567,6 +586,92 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     return HOPF_SUCCESS;
 }
 
+int check_mlp(const hopf_mlp *net) {
+    if (!net) return fail(HOPF_EINVAL, "null network");
+    if (net->n_in < 1 || net->hidden < 1 || net->n_out < 1 || net->hidden > 65536)
+        return fail(HOPF_EINVAL, "bad network sizes");
+    if (!net->w || !net->w_bf16 || !net->x_shift || !net->x_scale || !net->y_shift || !net->y_scale)
+        return fail(HOPF_EINVAL, "network pointers must be set");
+    return HOPF_SUCCESS;
+}
+
+int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *net, int P, const void *x_,
+                    const void *t_, int t_stride, int max_iter_warm, void *phi_, void *pstar_, void *gap_,
+                    int *iters, int *status, int *n_fallback, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const int n_inst = t_stride ? P : 1;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    SmallPlan sp;
+    if (t_stride == 0) sp = plan_small(dev, n, m, N, P);
+    const int tgrid = table_grid(dev, n_inst);
+    DevProblem d;
+    double *Tv, *i64, *tsc;
+    float *i32, *phat, *msc, *y;
+    int *list, *cnt, *ctr;
+    auto plan = [&](Arena &a) {
+        d = take_problem(a, n, m);
+        Tv = a.template take<double>(n_inst);
+        i64 = a.template take<double>((size_t)n_inst * L.stride);
+        i32 = a.template take<float>((size_t)n_inst * L.stride);
+        tsc = a.template take<double>((size_t)tgrid * table_scratch_doubles(n, m));
+        phat = a.template take<float>((size_t)P * n);
+        msc = a.template take<float>((size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, P, false));
+        list = a.template take<int>(P);
+        cnt = a.template take<int>(4);
+        ctr = a.template take<int>(4);
+        y = sp.ok ? nullptr : a.template take<float>((size_t)P * N * m);
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    rc = upload_problem(d, pr, s);
+    if (rc) return rc;
+    CU(launch_horizons(n_inst, s, t_, true, Tv));
+    rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
+    if (rc) return rc;
+    // prediction of p* from x
+    CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
+                   net->x_scale, net->y_shift, net->y_scale, P, (const float *)x_, phat, msc, false, s));
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.inst_stride = t_stride ? 1 : 0;
+    auto solve = [&](const SolveParams &pp, const float *pinit) -> int {
+        if (sp.ok) {
+            CU(cudaMemsetAsync(ctr, 0, sizeof(int), s));
+            CU(launch_pdhg_small(sp.NS, m, sp.grid, sp.threads, sp.smem, s, i32, pp, sp.ys_stride, (const float *)x_,
+                                 pinit, (float *)phi_, (float *)pstar_, (float *)gap_, iters, status, ctr));
+            return HOPF_SUCCESS;
+        }
+        return launch_generic<float>(i32, pp, (const float *)x_, pinit, (float *)phi_, (float *)pstar_,
+                                     (float *)gap_, iters, status, nullptr, nullptr, y, nullptr, s);
+    };
+    // warm solve, capped at max_iter_warm
+    SolveParams pw = prm;
+    pw.warm = 1;
+    pw.max_iter = max_iter_warm;
+    rc = solve(pw, phat);
+    if (rc) return rc;
+    // cold fallback for every point that the warm solve did not certify
+    CU(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    failed_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, status, list, cnt);
+    CU(cudaGetLastError());
+    SolveParams pc = prm;
+    pc.warm = 0;
+    pc.list = list;
+    pc.list_count = cnt;
+    rc = solve(pc, nullptr);
+    if (rc) return rc;
+    if (n_fallback) CU(cudaMemcpyAsync(n_fallback, cnt, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return HOPF_SUCCESS;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -637,6 +742,82 @@ int hopf_trajectory(const hopf_problem *prob, const hopf_opts *opts, int P, cons
     if (opts->precision == HOPF_FP64)
         return traj_impl<double>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
     return traj_impl<float>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
+}
+
+long long hopf_mlp_param_count(int n_in, int hidden, int n_out) { return mlp_param_count(n_in, hidden, n_out); }
+
+int hopf_mlp_sync(const hopf_mlp *net, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_mlp(net);
+    if (rc) return rc;
+    CU(mlp_sync_bf16(mlp_param_count(net->n_in, net->hidden, net->n_out), net->w, (__nv_bfloat16 *)net->w_bf16,
+                     (cudaStream_t)stream));
+    return HOPF_SUCCESS;
+}
+
+int hopf_mlp_forward(const hopf_mlp *net, int B, const float *x, float *y, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_mlp(net);
+    if (rc) return rc;
+    if (B < 0 || (B > 0 && (!x || !y))) return fail(HOPF_EINVAL, "bad batch or null array");
+    if (B == 0) return HOPF_SUCCESS;
+    void *base = nullptr;
+    rc = ensure_workspace(sizeof(float) * (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, false),
+                          &base);
+    if (rc) return rc;
+    CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
+                   net->x_scale, net->y_shift, net->y_scale, B, x, y, (float *)base, false, (cudaStream_t)stream));
+    return HOPF_SUCCESS;
+}
+
+int hopf_mlp_loss_grad(const hopf_mlp *net, int B, const float *x, const float *y, float *loss, float *grad,
+                       void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_mlp(net);
+    if (rc) return rc;
+    if (B < 1 || !x || !y || !loss || !grad) return fail(HOPF_EINVAL, "bad batch or null array");
+    void *base = nullptr;
+    rc = ensure_workspace(sizeof(float) * (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, true),
+                          &base);
+    if (rc) return rc;
+    CU(mlp_loss_grad(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
+                     net->x_scale, net->y_shift, net->y_scale, B, x, y, loss, grad, (float *)base,
+                     (cudaStream_t)stream));
+    return HOPF_SUCCESS;
+}
+
+int hopf_mlp_adam(const hopf_mlp *net, const float *grad, int step, double lr, double beta1, double beta2,
+                  double eps, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_mlp(net);
+    if (rc) return rc;
+    if (!net->adam_m || !net->adam_v || !grad || step < 1) return fail(HOPF_EINVAL, "Adam needs moments, grad, step>=1");
+    CU(mlp_adam(mlp_param_count(net->n_in, net->hidden, net->n_out), net->w, (__nv_bfloat16 *)net->w_bf16, grad,
+                net->adam_m, net->adam_v, (float)lr, (float)beta1, (float)beta2, (float)eps, step,
+                (cudaStream_t)stream));
+    return HOPF_SUCCESS;
+}
+
+int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_mlp *net, int P, const void *x,
+                    const void *t, int t_stride, int max_iter_warm, void *phi, void *p_star, void *gap, int *iters,
+                    int *status, int *n_fallback, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_problem(prob, opts, true);
+    if (rc) return rc;
+    rc = check_mlp(net);
+    if (rc) return rc;
+    if (opts->precision != HOPF_FP32 || opts->host_io) return fail(HOPF_EINVAL, "warm start: FP32 device arrays only");
+    if (net->n_in != prob->n || net->n_out != prob->n) return fail(HOPF_EINVAL, "network must map R^n to R^n");
+    if (P < 0 || (t_stride != 0 && t_stride != 1) || max_iter_warm < 0) return fail(HOPF_EINVAL, "bad P/t_stride");
+    if (P == 0) return HOPF_SUCCESS;
+    if (!x || !t || !phi || !p_star || !gap || !iters || !status) return fail(HOPF_EINVAL, "null array");
+    return value_warm_impl(prob, opts, net, P, x, t, t_stride, max_iter_warm, phi, p_star, gap, iters, status,
+                           n_fallback, (cudaStream_t)stream);
 }
 
 const char *hopf_status_string(int code) {

@@ -48,6 +48,8 @@ struct SolveParams {
     int sign_mode;     // time-to-reach: stop once the sign of phi is certified
     int inst_stride;   // 0: one shared instance, 1: instance k for point k
     int accel;         // Chambolle-Pock accelerated variant (strongly convex G)
+    const int *list;        // optional: solve only the points list[0 .. *list_count)
+    const int *list_count;  // device count for `list`
     double tau, tol_gap, sign_floor;
 };
 

@@ -174,7 +174,7 @@ int run(const hopf_problem *pr, const hopf_opts *o, int P, const void *x, const 
     if (launch_build_instances(tgrid, n >= 24 ? 256 : 64, s, A, B, q, W, Tv, nullptr, n_inst, n, m, N, o->rule,
                                o->tau, o->sigma_scale, i64, i32, tsc) != cudaSuccess)
         return HOPF_ECUDA;
-    SolveParams prm;
+    SolveParams prm{};
     prm.n = n;
     prm.m = m;
     prm.N = N;

@@ -44,8 +44,13 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     const int n = prm.n, m = prm.m, N = prm.N;
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * warps + warp;
-    if (k >= prm.P) return;                       // uniform per warp
+    int k = blockIdx.x * warps + warp;
+    if (prm.list) {
+        if (k >= *prm.list_count) return;        // uniform per warp
+        k = prm.list[k];
+    } else if (k >= prm.P) {
+        return;
+    }
     if (active && !active[k]) return;
     extern __shared__ unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 6 * n;

@@ -90,7 +90,8 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                   int *__restrict__ iters, int *__restrict__ status, int *__restrict__ counter) {
     static_assert(32 % TPP == 0, "groups must tile a warp");
     constexpr int KR = KRow<MS, NS>::stride;
-    const int n = prm.n, N = prm.N, P = prm.P;
+    const int n = prm.n, N = prm.N;
+    const int P = prm.list ? *prm.list_count : prm.P;   // number of points to take
     const InstanceLayout L = InstanceLayout::make(n, prm.m, N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *Ks = reinterpret_cast<float *>(smem_raw);
@@ -155,7 +156,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             if (q == 0) nx = atomicAdd(counter, 1);
             nx = __shfl_sync(gmask, nx, lead);
             if (nx >= P) { idle = true; pt = -1; return; }
-            pt = nx;
+            pt = prm.list ? prm.list[nx] : nx;
             __syncwarp(gmask);
             if (q == 0) {
 #pragma unroll

@@ -39,10 +39,16 @@ def test_struct_layout_matches_header():
     # field order and types of the ctypes mirror follow the header's structs
     from paper_1712_08226_gb300 import _lib
     src = open(os.path.join(ROOT, "include", "hopf.h")).read()
-    for cname, py in (("hopf_problem", _lib.HopfProblem), ("hopf_opts", _lib.HopfOpts)):
+    for cname, py in (("hopf_problem", _lib.HopfProblem), ("hopf_opts", _lib.HopfOpts),
+                      ("hopf_mlp", _lib.HopfMlp)):
         body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + cname + ";", src, re.S).group(1)
-        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-        fields = re.findall(r"([A-Za-z_]+)\s*;", re.sub(r"\*", " ", body))
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S).replace("*", " ")
+        fields = []
+        for decl in body.split(";"):
+            for piece in decl.split(","):
+                names = re.findall(r"[A-Za-z_][A-Za-z_0-9]*", piece)
+                if names:
+                    fields.append(names[-1])
         assert fields == [f[0] for f in py._fields_], (cname, fields)
 
 
