@@ -4,8 +4,13 @@ Workload (one step): the batched FP32 value solve of the generalized Hopf
 formula for 65,536 query points x ~ N(0, 4 I) of one random n=10, m=2 system
 (A ~ N(0, 1/n) - 0.5 I, B ~ N(0, 1), unit-ball control, ellipsoid target
 Q = diag U[1, 4]) at horizon t = 2 with 256 left-Riemann nodes: node-table
-build + persistent primal-dual kernel, every point certified to relative gap
-<= 1e-5.  Inputs are seeded and synthetic.
+build, warm-start network prediction of p*, persistent primal-dual kernel
+(accelerated steps, two phases) from the prediction, and a cold re-solve of
+any point the warm solve leaves uncertified; every point is certified to
+relative gap <= 1e-5.  The network is trained before timing on 262,144 other
+points labelled by the solver itself.  The same line reports the cold-start
+solves (the paper's iteration of Eq. 15, and the accelerated one) on the same
+GB300 for comparison.  Inputs are seeded and synthetic.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own 65,536 points (weak scaling, no
@@ -32,6 +37,8 @@ METRIC = "Hopf solves/sec at gap<=1e-5: warm-start batched vs plain cold PDHG, s
 POINTS = 65536
 TOL = 1e-5
 TAU_ACCEL = 2.0
+TRAIN_POINTS = 262144
+TRAIN_EPOCHS = 60
 
 
 def rank_env():
@@ -144,6 +151,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def train_warm_start(H, sysd, w, rank):
+    """Untimed set-up: label 262,144 fresh points with the GPU solver (cold,
+    accelerated, gap 2e-6) and train the warm-start network on them with the
+    library's own forward/backward/Adam kernels."""
+    import torch
+    from paper_1712_08226_gb300.warmstart import WarmStartNet
+    t0 = time.perf_counter()
+    xtr = torch.tensor(wl.normal_points(40 + 1000 * rank, TRAIN_POINTS, 10, 2.0), dtype=torch.float32,
+                       device="cuda")
+    lab = H.value(sysd, xtr, w["t"], H.Options(N=w["N"], tau=TAU_ACCEL, tol_gap=2e-6, accel=True))
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    net = WarmStartNet(10, 10, hidden=256, seed=0)
+    net.set_normalisation(xtr, lab["p"])
+    t0 = time.perf_counter()
+    hist = net.fit(xtr, lab["p"], epochs=TRAIN_EPOCHS, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    info = {"train_points": TRAIN_POINTS, "label_s": round(t_label, 2), "epochs": TRAIN_EPOCHS, "batch": 4096,
+            "train_s": round(time.perf_counter() - t0, 2), "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+            "network": "10-256-256-10 GELU, bf16 weights, fp32 accumulation"}
+    return net, info
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -153,7 +183,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=POINTS, help="points per GPU (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain (Eq. 15) comparison run")
+    ap.add_argument("--no-compare", action="store_true", help="skip the cold-start comparison runs")
+    ap.add_argument("--cold", action="store_true", help="time the cold accelerated solve instead of the warm one")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -177,6 +208,7 @@ def main():
         dist.init_process_group("nccl", init_method="env://", device_id=torch.device("cuda", local))
     import paper_1712_08226_gb300 as H
     from paper_1712_08226_gb300 import build
+    from paper_1712_08226_gb300.warmstart import value_warm
     if rank == 0:
         build.build()
     if dist:
@@ -187,29 +219,35 @@ def main():
     w = workload(rank, points)
     sysd = H.System.from_dict(w["system"])
     n, m, N = 10, 2, w["N"]
-    # cold start, accelerated primal-dual steps (strongly convex G), tau0 = 2
-    opts = H.Options(N=N, rule=H.LEFT_RIEMANN, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8,
-                     precision=H.FP32, profile=True, accel=True)
-    # the paper's iteration (Eq. 15, theta = 1) from the same cold start
-    opts_plain = H.Options(N=N, rule=H.LEFT_RIEMANN, tau=w["tau"], tol_gap=TOL, max_iter=100000, gap_every=8,
-                           precision=H.FP32, profile=True, accel=False)
     x_dev = torch.tensor(w["x"], dtype=torch.float32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    # cold start, accelerated steps (strongly convex G), tau0 = 2
+    opts_cold = H.Options(N=N, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                          profile=True, accel=True, park_iters=1024)
+    # the paper's iteration (Eq. 15, theta = 1) from the same cold start
+    opts_plain = H.Options(N=N, tau=w["tau"], tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                           profile=True, accel=False, park_iters=512)
+    # warm start from the network, accelerated steps, cold fallback
+    opts_warm = H.Options(N=N, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                          profile=True, accel=True, park_iters=512)
 
-    for _ in range(args.warmup):
-        H.value(sysd, x_dev, w["t"], opts)
-    torch.cuda.synchronize()
+    net, train_info = (None, None) if args.cold else train_warm_start(H, sysd, w, rank)
 
-    def timed(o, steps):
+    def call(kind):
+        if kind == "warm":
+            return value_warm(sysd, x_dev, w["t"], net, opts_warm)
+        return H.value(sysd, x_dev, w["t"], opts_cold if kind == "cold" else opts_plain)
+
+    def timed(kind, steps):
         """Device time per step (CUDA events on the launching stream), L2 flushed before each."""
-        ms, sv, tb, un, okc, iters_all = [], [], [], 0, 0, None
+        ms, sv, tb, un, okc, iters_all, fb = [], [], [], 0, 0, None, 0
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r = H.value(sysd, x_dev, w["t"], o)
+            r = call(kind)
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -220,34 +258,47 @@ def main():
             un += int((it + 1).sum().item())
             okc += int((r["status"] == 0).sum().item())
             iters_all = it.cpu().numpy()
-        return ms, sv, tb, un, okc, iters_all
+            if "n_fallback" in r:
+                fb = int(r["n_fallback"].item())
+        return dict(ms=ms, solve_ms=sv, pre_ms=tb, units=un, ok=okc, iters=iters_all, fallback=fb)
 
-    plain = None
-    if not args.no_plain:
-        H.value(sysd, x_dev, w["t"], opts_plain)
-        pm, psv, _, pun, pok, pit = timed(opts_plain, max(1, min(3, args.steps)))
-        plain = {"solves_per_s": pok / len(pm) / (statistics.mean(pm) * 1e-3), "ms_per_step": statistics.mean(pm),
-                 "tau": w["tau"], "mean_iters": float(pit.mean()), "max_iters": int(pit.max()),
-                 "steps": len(pm)}
+    main_kind = "cold" if args.cold else "warm"
+    for _ in range(args.warmup):
+        call(main_kind)
+    torch.cuda.synchronize()
+
+    compare = {}
+    if not args.no_compare:
+        for kind in ("plain", "cold") if main_kind == "warm" else ("plain",):
+            call(kind)
+            rr = timed(kind, max(1, min(3, args.steps)))
+            compare[kind] = {"solves_per_s": rr["ok"] / len(rr["ms"]) / (statistics.mean(rr["ms"]) * 1e-3),
+                             "ms_per_step": statistics.mean(rr["ms"]), "mean_iters": float(rr["iters"].mean()),
+                             "max_iters": int(rr["iters"].max()), "steps": len(rr["ms"])}
 
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, solve_ms, table_ms, units, ok, iters_last = timed(opts, args.steps)
+    res = timed(main_kind, args.steps)
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist:
         dist.barrier()
+    step_ms, solve_ms, pre_ms, units, ok, iters_last = (res["ms"], res["solve_ms"], res["pre_ms"], res["units"],
+                                                        res["ok"], res["iters"])
 
-    # end to end through the C ABI with host buffers (pinned), copies included
+    # end to end through the C ABI with host buffers (pinned), copies inside the call
     x_pin = torch.tensor(w["x"], dtype=torch.float32).pin_memory()
     x_host = x_pin.numpy()
     e2e_s, ok_e2e = [], 0
     for i in range(0 if args.no_e2e else args.warmup + args.steps):
         t0 = time.perf_counter()
-        rh = H.value(sysd, x_host, w["t"], opts)
+        if main_kind == "warm":
+            rh = value_warm(sysd, x_host, w["t"], net, opts_warm)
+        else:
+            rh = H.value(sysd, x_host, w["t"], opts_cold)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             e2e_s.append(dt)
@@ -256,7 +307,6 @@ def main():
         e2e_s = [float("nan")]
 
     mean_ms = statistics.mean(step_ms)
-    POINTS_ = points
     t_local = np.array([mean_ms, statistics.mean(e2e_s) * 1e3], dtype=np.float64)
     if dist:
         tt = torch.tensor(t_local, device="cuda")
@@ -275,29 +325,32 @@ def main():
     sms = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x max SM clock
-    h2d = POINTS_ * n * 4 + 4
-    d2h = POINTS_ * (4 + 4 * n + 4 + 4 + 4)
+    h2d = points * n * 4 + 4
+    d2h = points * (4 + 4 * n + 4 + 4 + 4) + (4 if main_kind == "warm" else 0)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(t_local[0]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; random n=10 system, x~N(0,4I))",
-        "config": {"workload": f"random_n10_m2_t2_N256_{POINTS_}pts", "n": n, "m": m, "N": N, "t": w["t"],
-                   "points_per_gpu": POINTS_, "tol_gap": TOL, "tau0": TAU_ACCEL,
-                   "start": "cold", "iteration": "accelerated (strongly convex G)",
+        "config": {"workload": f"random_n10_m2_t2_N256_{points}pts", "n": n, "m": m, "N": N, "t": w["t"],
+                   "points_per_gpu": points, "tol_gap": TOL, "tau0": TAU_ACCEL,
+                   "start": "warm (network prediction), cold fallback" if main_kind == "warm" else "cold",
+                   "iteration": "accelerated (strongly convex G), two-phase",
                    "l2": "flushed between timed steps (512 MB write)",
                    "mean_iters": float(iters_last.mean()), "p99_iters": float(np.percentile(iters_last, 99)),
-                   "max_iters": int(iters_last.max()),
+                   "max_iters": int(iters_last.max()), "fallback_points": res["fallback"],
                    "certified_per_step": solves_per_step,
-                   "ms_tables": statistics.mean(table_ms), "ms_solve": statistics.mean(solve_ms),
-                   "plain_cold_eq15": plain},
-        "roofline": {"bound": "alu", "kernel": "pdhg_small_kernel<10,2,4>", "achieved": achieved,
+                   "ms_tables_and_prediction": statistics.mean(pre_ms), "ms_solve": statistics.mean(solve_ms),
+                   "warm_start_training": train_info,
+                   "cold_start_comparison": compare},
+        "roofline": {"bound": "alu", "kernel": "pdhg_small_kernel<10,2,4> + <10,2,32>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
+                     "flops_per_point_iter": fpi,
                      "point_iters_per_s": units / args.steps / (statistics.mean(solve_ms) * 1e-3)},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (9 if main_kind == "warm" else 5) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

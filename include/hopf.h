@@ -107,6 +107,11 @@ typedef struct {
                            theta = 1/sqrt(1 + 2 gamma tau), tau *= theta,
                            sigma /= theta, pbar = p + theta (p - p_old).  The
                            starting tau is opts->tau.                             */
+    int park_iters;     /* small-state float32 solves run in two phases: 4 lanes
+                           per point, then points still uncertified after
+                           park_iters iterations continue with 32 lanes per
+                           point (lower latency for the slowest points).
+                           0 = library default (1024); < 0 = one phase only.      */
 } hopf_opts;
 
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,
@@ -235,8 +240,11 @@ int hopf_mlp_adam(const hopf_mlp *net, const float *grad, int step, double lr, d
  * as the warm start p_init.  Each warm solve runs at most max_iter_warm
  * iterations; a point that is not certified (status != HOPF_OK) is solved
  * again from the cold start with opts->max_iter, and its outputs are those of
- * the cold solve.  Outputs as in hopf_value.  n_fallback: NULL or a device
- * int that receives the number of points solved again.
+ * the cold solve.  Outputs as in hopf_value (host arrays when opts->host_io;
+ * the network's parameters are always device arrays).  n_fallback: NULL or an
+ * int (device, or host when opts->host_io) that receives the number of points
+ * solved again.  With opts->profile, hopf_last_profile reports the table build
+ * plus network prediction as ms_tables and both solves as ms_solve.
  */
 int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_mlp *net, int P,
                     const void *x, const void *t, int t_stride, int max_iter_warm,

@@ -64,11 +64,12 @@ class Options:
     tol_T: float = 1e-5
     profile: bool = False
     accel: bool = False
+    park_iters: int = 0
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
-                             int(self.profile), int(self.accel))
+                             int(self.profile), int(self.accel), int(self.park_iters))
 
 
 def _is_torch(a):

@@ -24,7 +24,7 @@ template <typename R>
 cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
                                 R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
                                 const int *active, cudaStream_t s);
-cudaError_t launch_pdhg_small(int NS, int m, int grid, int threads, size_t smem, cudaStream_t s,
+cudaError_t launch_pdhg_small(int NS, int m, int tpp, int grid, int threads, size_t smem, cudaStream_t s,
                               const float *inst, const SolveParams &prm, int ys_stride, const float *x,
                               const float *p_init, float *phi, float *pstar, float *gap, int *iters,
                               int *status, int *counter);
@@ -243,17 +243,22 @@ int upload_problem(const DevProblem &d, const hopf_problem *pr, cudaStream_t s) 
 int table_threads(int n) { return n >= 24 ? 256 : 64; }
 
 // ------------------------------------------------------------ small kernel
-constexpr int SMALL_TPP = 4;
 constexpr int SMALL_MAX_THREADS = 384;
+// Two-phase solve: points not certified after this many iterations of the
+// throughput phase (4 lanes per point) are finished by the latency phase
+// (32 lanes per point).
+constexpr int SMALL_PARK_ITERS = 1024;
 
 struct SmallPlan {
     bool ok = false;
-    int NS = 0, pts = 0, threads = 0, ys_stride = 0, grid = 0;
+    int NS = 0, pts = 0, threads = 0, ys_stride = 0, grid = 0, tpp = 4;
     size_t smem = 0;
 };
 
-SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
+SmallPlan plan_small(const Device &dev, int n, int m, int N, int P, int tpp = 4) {
+    const int SMALL_TPP = tpp;
     SmallPlan sp;
+    sp.tpp = tpp;
     if (n > 16 || m > 2) return sp;
     sp.NS = (n + 1) & ~1;
     const int KR = (m * sp.NS + 1 + 3) & ~3;
@@ -266,8 +271,8 @@ SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
     if (fixed + 8 * per_pt > budget) return sp;
     int pts = (int)((budget - fixed) / per_pt);
     pts = std::min(pts, SMALL_MAX_THREADS / SMALL_TPP);
-    pts -= pts % (32 / SMALL_TPP);
-    if (pts < 32 / SMALL_TPP) return sp;
+    pts -= pts % std::max(1, 32 / SMALL_TPP);
+    if (pts < std::max(1, 32 / SMALL_TPP)) return sp;
     sp.pts = pts;
     sp.threads = pts * SMALL_TPP;
     sp.smem = fixed + (size_t)pts * per_pt;
@@ -275,6 +280,47 @@ SmallPlan plan_small(const Device &dev, int n, int m, int N, int P) {
     sp.grid = std::max(1, std::min(dev.sms, want));
     sp.ok = true;
     return sp;
+}
+
+struct CarryBufs {
+    float *y = nullptr, *st = nullptr;
+    int *list = nullptr, *count = nullptr, *ctr = nullptr;
+};
+
+template <typename AR>
+CarryBufs take_carry(AR &a, int P, int N, int m) {
+    CarryBufs cb;
+    cb.y = a.template take<float>((size_t)P * N * m);
+    cb.st = a.template take<float>((size_t)P * CARRY_W);
+    cb.list = a.template take<int>(P);
+    cb.count = a.template take<int>(4);
+    cb.ctr = a.template take<int>(4);
+    return cb;
+}
+
+// Throughput phase (4 lanes per point) that parks slow points, then the
+// latency phase (32 lanes per point) that finishes them.
+int run_small_two_phase(const SmallPlan &sp, const SmallPlan &sp32, int m, const float *inst, SolveParams prm,
+                        const float *x, const float *pinit, float *phi, float *pstar, float *gap, int *iters,
+                        int *status, const CarryBufs &cb, int park_iters, cudaStream_t s) {
+    CU(cudaMemsetAsync(cb.ctr, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(cb.count, 0, sizeof(int), s));
+    const bool two = sp32.ok && park_iters >= 0;
+    prm.carry_cap = two ? (park_iters > 0 ? park_iters : SMALL_PARK_ITERS) : 0;
+    prm.carry_in = 0;
+    prm.carry_y = cb.y;
+    prm.carry_st = cb.st;
+    prm.carry_list = cb.list;
+    prm.carry_count = cb.count;
+    CU(launch_pdhg_small(sp.NS, m, sp.tpp, sp.grid, sp.threads, sp.smem, s, inst, prm, sp.ys_stride, x, pinit, phi,
+                         pstar, gap, iters, status, cb.ctr));
+    if (!two) return HOPF_SUCCESS;
+    CU(cudaMemsetAsync(cb.ctr + 1, 0, sizeof(int), s));
+    prm.carry_cap = 0;
+    prm.carry_in = 1;
+    CU(launch_pdhg_small(sp32.NS, m, sp32.tpp, sp32.grid, sp32.threads, sp32.smem, s, inst, prm, sp32.ys_stride, x,
+                         pinit, phi, pstar, gap, iters, status, cb.ctr + 1));
+    return HOPF_SUCCESS;
 }
 
 void fill_params(SolveParams &prm, const hopf_problem *pr, const hopf_opts *o, int P) {
@@ -325,10 +371,15 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     int rc = query_device(&dev);
     if (rc) return rc;
     const InstanceLayout L = InstanceLayout::make(n, m, N);
-    SmallPlan sp;
-    if (fp32 && t_stride == 0) sp = plan_small(dev, n, m, N, P);
+    SmallPlan sp, sp32;
+    if (fp32 && t_stride == 0) {
+        sp = plan_small(dev, n, m, N, P);
+        sp32 = plan_small(dev, n, m, N, P, 32);
+        sp32.grid = dev.sms;
+    }
     const int tgrid = table_grid(dev, n_inst);
     const bool hio = o->host_io != 0;
+    CarryBufs cb;
 
     auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
                     R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
@@ -348,6 +399,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         dst = hio ? a.template take<int>(P) : status;
         y = sp.ok ? nullptr : a.template take<R>((size_t)P * N * m);
         ctr = a.template take<int>(4);
+        if (sp.ok) cb = take_carry(a, P, N, m);
     };
     DevProblem d;
     double *Tv, *i64, *tsc;
@@ -391,10 +443,9 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     prm.inst_stride = t_stride ? 1 : 0;
     const R *inst = fp32 ? (const R *)i32 : (const R *)i64;
     if (sp.ok) {
-        CU(cudaMemsetAsync(ctr, 0, sizeof(int), s));
-        CU(launch_pdhg_small(sp.NS, m, sp.grid, sp.threads, sp.smem, s, (const float *)inst, prm, sp.ys_stride,
-                             (const float *)dx, (const float *)dpi, (float *)dphi, (float *)dps, (float *)dgap,
-                             dit, dst, ctr));
+        rc = run_small_two_phase(sp, sp32, m, (const float *)inst, prm, (const float *)dx, (const float *)dpi,
+                                 (float *)dphi, (float *)dps, (float *)dgap, dit, dst, cb, o->park_iters, s);
+        if (rc) return rc;
     } else {
         rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
         if (rc) return rc;
@@ -604,15 +655,30 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     int rc = query_device(&dev);
     if (rc) return rc;
     const InstanceLayout L = InstanceLayout::make(n, m, N);
-    SmallPlan sp;
-    if (t_stride == 0) sp = plan_small(dev, n, m, N, P);
+    SmallPlan sp, sp32;
+    if (t_stride == 0) {
+        sp = plan_small(dev, n, m, N, P);
+        sp32 = plan_small(dev, n, m, N, P, 32);
+        sp32.grid = dev.sms;
+    }
     const int tgrid = table_grid(dev, n_inst);
     DevProblem d;
     double *Tv, *i64, *tsc;
     float *i32, *phat, *msc, *y;
     int *list, *cnt, *ctr;
+    CarryBufs cb;
+    const bool hio = o->host_io != 0;
+    float *dx, *dt, *dphi, *dps, *dgap;
+    int *dit, *dst;
     auto plan = [&](Arena &a) {
         d = take_problem(a, n, m);
+        dx = hio ? a.template take<float>((size_t)P * n) : (float *)x_;
+        dt = hio ? a.template take<float>((size_t)n_inst) : (float *)t_;
+        dphi = hio ? a.template take<float>(P) : (float *)phi_;
+        dps = hio ? a.template take<float>((size_t)P * n) : (float *)pstar_;
+        dgap = hio ? a.template take<float>(P) : (float *)gap_;
+        dit = hio ? a.template take<int>(P) : iters;
+        dst = hio ? a.template take<int>(P) : status;
         Tv = a.template take<double>(n_inst);
         i64 = a.template take<double>((size_t)n_inst * L.stride);
         i32 = a.template take<float>((size_t)n_inst * L.stride);
@@ -623,6 +689,7 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         cnt = a.template take<int>(4);
         ctr = a.template take<int>(4);
         y = sp.ok ? nullptr : a.template take<float>((size_t)P * N * m);
+        if (sp.ok) cb = take_carry(a, P, N, m);
     };
     Arena meas(nullptr);
     plan(meas);
@@ -633,24 +700,36 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     plan(a);
     rc = upload_problem(d, pr, s);
     if (rc) return rc;
-    CU(launch_horizons(n_inst, s, t_, true, Tv));
+    if (hio) {
+        CU(cudaMemcpyAsync(dx, x_, sizeof(float) * P * n, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dt, t_, sizeof(float) * n_inst, cudaMemcpyHostToDevice, s));
+    }
+    const bool prof = o->profile != 0;
+    if (prof) {
+        if (g_prof.device != dev.id) {
+            for (auto &e : g_prof.ev)
+                if (e) cudaEventDestroy(e);
+            for (auto &e : g_prof.ev) CU(cudaEventCreate(&e));
+            g_prof.device = dev.id;
+        }
+        g_prof.valid = false;
+        CU(cudaEventRecord(g_prof.ev[0], s));
+    }
+    CU(launch_horizons(n_inst, s, dt, true, Tv));
     rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
     if (rc) return rc;
     // prediction of p* from x
     CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
-                   net->x_scale, net->y_shift, net->y_scale, P, (const float *)x_, phat, msc, false, s));
+                   net->x_scale, net->y_shift, net->y_scale, P, dx, phat, msc, false, s));
+    if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     SolveParams prm;
     fill_params(prm, pr, o, P);
     prm.inst_stride = t_stride ? 1 : 0;
     auto solve = [&](const SolveParams &pp, const float *pinit) -> int {
-        if (sp.ok) {
-            CU(cudaMemsetAsync(ctr, 0, sizeof(int), s));
-            CU(launch_pdhg_small(sp.NS, m, sp.grid, sp.threads, sp.smem, s, i32, pp, sp.ys_stride, (const float *)x_,
-                                 pinit, (float *)phi_, (float *)pstar_, (float *)gap_, iters, status, ctr));
-            return HOPF_SUCCESS;
-        }
-        return launch_generic<float>(i32, pp, (const float *)x_, pinit, (float *)phi_, (float *)pstar_,
-                                     (float *)gap_, iters, status, nullptr, nullptr, y, nullptr, s);
+        if (sp.ok)
+            return run_small_two_phase(sp, sp32, m, i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, cb,
+                                       o->park_iters, s);
+        return launch_generic<float>(i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
     };
     // warm solve, capped at max_iter_warm
     SolveParams pw = prm;
@@ -660,7 +739,7 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     if (rc) return rc;
     // cold fallback for every point that the warm solve did not certify
     CU(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    failed_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, status, list, cnt);
+    failed_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dst, list, cnt);
     CU(cudaGetLastError());
     SolveParams pc = prm;
     pc.warm = 0;
@@ -668,7 +747,20 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     pc.list_count = cnt;
     rc = solve(pc, nullptr);
     if (rc) return rc;
-    if (n_fallback) CU(cudaMemcpyAsync(n_fallback, cnt, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    if (prof) {
+        CU(cudaEventRecord(g_prof.ev[2], s));
+        g_prof.valid = true;
+    }
+    if (n_fallback)
+        CU(cudaMemcpyAsync(n_fallback, cnt, sizeof(int), hio ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (hio) {
+        CU(cudaMemcpyAsync(phi_, dphi, sizeof(float) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(pstar_, dps, sizeof(float) * P * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(gap_, dgap, sizeof(float) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(iters, dit, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status, dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
     return HOPF_SUCCESS;
 }
 
@@ -811,7 +903,7 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
     if (rc) return rc;
     rc = check_mlp(net);
     if (rc) return rc;
-    if (opts->precision != HOPF_FP32 || opts->host_io) return fail(HOPF_EINVAL, "warm start: FP32 device arrays only");
+    if (opts->precision != HOPF_FP32) return fail(HOPF_EINVAL, "warm start: FP32 only");
     if (net->n_in != prob->n || net->n_out != prob->n) return fail(HOPF_EINVAL, "network must map R^n to R^n");
     if (P < 0 || (t_stride != 0 && t_stride != 1) || max_iter_warm < 0) return fail(HOPF_EINVAL, "bad P/t_stride");
     if (P == 0) return HOPF_SUCCESS;

@@ -50,6 +50,15 @@ struct SolveParams {
     int accel;         // Chambolle-Pock accelerated variant (strongly convex G)
     const int *list;        // optional: solve only the points list[0 .. *list_count)
     const int *list_count;  // device count for `list`
+    // two-phase solve of the small kernel: the throughput phase parks every
+    // point still uncertified after carry_cap iterations (carry_cap > 0); the
+    // latency phase (carry_in = 1) resumes the parked points
+    int carry_cap;
+    int carry_in;
+    float *carry_y;         // [slot][N m] parked dual variables
+    float *carry_st;        // [slot][CARRY_W] p, pbar, tau, sigma, iteration count
+    int *carry_list;        // point index of each slot
+    int *carry_count;       // number of parked points
     double tau, tol_gap, sign_floor;
 };
 
@@ -57,6 +66,8 @@ struct SolveParams {
 __host__ __device__ inline long long table_scratch_doubles(int n, int m) {
     return 9LL * n * n + 2LL * n * m + 2LL * n + 16;
 }
+
+constexpr int CARRY_W = 40;   // p [16], pbar [16], tau, sigma, iteration count, pad
 
 enum { SC_SIGMA = 0, SC_T = 1, SC_L2 = 2, SC_ZERO = 3, SC_GAMMA = 4 };
 

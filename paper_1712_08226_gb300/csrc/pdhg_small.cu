@@ -54,9 +54,13 @@ __device__ __forceinline__ void node_pass(const float *__restrict__ Ks, float *_
         float tn = 0.f, un = 0.f;
 #pragma unroll
         for (int c = 0; c < MS; ++c) {
-            float t = 0.f;
+            float t0 = 0.f, t1 = 0.f;       // two partial sums: half-length FMA chains
 #pragma unroll
-            for (int j = 0; j < NS; ++j) t = fmaf(kf[c * NS + j], pb[j], t);
+            for (int j = 0; j < NS; j += 2) {
+                t0 = fmaf(kf[c * NS + j], pb[j], t0);
+                if (j + 1 < NS) t1 = fmaf(kf[c * NS + j + 1], pb[j + 1], t1);
+            }
+            const float t = t0 + t1;
             if (CHECK) tn = ball ? fmaf(t, t, tn) : tn + fabsf(t);
             u[c] = fmaf(sigma, t, u[c]);
             un = fmaf(u[c], u[c], un);
@@ -144,10 +148,11 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
     float *x0 = X0s + (size_t)slot * NS;
 
     float p[NS], pb[NS], acc[NS];
-    int pt = -1, it_pt = 0;
+    int pt = -1, it_pt = 0, slot_in = -1;
     bool idle = false, have_D = false, fresh = false;
     float Dprev = 0.f;
     float tau = tau0, sigma = sigma0;      // current steps (they change only when accelerated)
+    const int n_carry = prm.carry_in ? *prm.carry_count : 0;
 
     // take the next point for this group; T = 0 points finish on the spot
     auto fetch = [&]() {
@@ -155,8 +160,9 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             int nx = 0;
             if (q == 0) nx = atomicAdd(counter, 1);
             nx = __shfl_sync(gmask, nx, lead);
-            if (nx >= P) { idle = true; pt = -1; return; }
-            pt = prm.list ? prm.list[nx] : nx;
+            if (nx >= (prm.carry_in ? n_carry : P)) { idle = true; pt = -1; return; }
+            slot_in = nx;
+            pt = prm.carry_in ? prm.carry_list[nx] : (prm.list ? prm.list[nx] : nx);
             __syncwarp(gmask);
             if (q == 0) {
 #pragma unroll
@@ -176,6 +182,26 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             if (q == 0) {
                 phi[pt] = J; gap_out[pt] = 0.f; iters[pt] = 0; status[pt] = HOPF_OK;
             }
+        }
+        have_D = false;
+        fresh = true;
+        if (prm.carry_in) {
+            // resume a point parked by the throughput phase: primal state, step
+            // sizes, iteration count and the dual variable y
+            const float *st = prm.carry_st + (size_t)slot_in * CARRY_W;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                p[j] = st[j];
+                pb[j] = st[16 + j];
+            }
+            tau = st[32];
+            sigma = st[33];
+            it_pt = __float_as_int(st[34]);
+            const float *cy = prm.carry_y + (size_t)slot_in * N * MS;
+            for (int i = q; i < N; i += TPP)
+#pragma unroll
+                for (int c = 0; c < MS; ++c) ys[i * MS + c] = cy[(size_t)i * MS + c];
+            return;
         }
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
@@ -209,18 +235,18 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             for (int c = 0; c < MS; ++c) ys[i * MS + c] = t[c];
         }
         it_pt = 0;
-        have_D = false;
-        fresh = true;
         tau = tau0;
         sigma = sigma0;
     };
 
     fetch();
+    fresh = false;            // the first iteration of the first point is a full one
     int wit = 0;
     for (;;) {
         ++wit;
         ++it_pt;
         const bool check = (wit % g) == 0;
+        bool park = false;
         float hs = 0.f;
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = 0.f;
@@ -260,6 +286,8 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                         status[pt] = bad ? HOPF_NONFINITE : (conv ? HOPF_OK : HOPF_MAXITER);
                     }
                     fetch();
+                } else if (prm.carry_cap > 0 && it_pt - 1 >= prm.carry_cap) {
+                    park = true;       // hand over to the latency phase after this step
                 }
             }
             if (__all_sync(0xffffffffu, idle)) break;
@@ -269,7 +297,30 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
 #pragma unroll
             for (int b = 0; b < NS; ++b) v[b] = fmaf(-tau, acc[b], fmaf(tau, x0[b], p[b]));
             float th = 1.f;
-            if (accel) {
+            if constexpr (TPP >= NS) {
+                // one lane per row of the n x n products, rows gathered by shuffles
+                const int a = q < NS ? q : 0;
+                float r = 0.f;
+                if (accel) {
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) r = fmaf(Us[b * NS + a], v[b], r);
+                    r = __fdividef(r, fmaf(0.5f * tau, lams[a], 1.f));
+                    float z[NS];
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) z[b] = __shfl_sync(gmask, r, lead + b);
+                    r = 0.f;
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) r = fmaf(Us[a * NS + b], z[b], r);
+                    th = rsqrtf(fmaf(2.f * gamma, tau, 1.f));
+                    tau *= th;
+                    sigma /= th;
+                } else {
+#pragma unroll
+                    for (int b = 0; b < NS; ++b) r = fmaf(Ss[a * NS + b], v[b], r);
+                }
+#pragma unroll
+                for (int b = 0; b < NS; ++b) pn[b] = __shfl_sync(gmask, r, lead + b);
+            } else if (accel) {
                 // (I + tau M/2)^-1 v = U diag(1 / (1 + tau lam / 2)) U^T v
                 float z[NS];
 #pragma unroll
@@ -303,7 +354,30 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                 pb[j] = fmaf(th, pn[j] - p[j], pn[j]);
                 p[j] = pn[j];
             }
-            if (((wit + 1) % g) == 0) {
+            if (park) {
+                // save the point after this full step and take a new one
+                int slot = 0;
+                if (q == 0) slot = atomicAdd(prm.carry_count, 1);
+                slot = __shfl_sync(gmask, slot, lead);
+                float *cy = prm.carry_y + (size_t)slot * N * MS;
+                for (int i = q; i < N; i += TPP)
+#pragma unroll
+                    for (int c = 0; c < MS; ++c) cy[(size_t)i * MS + c] = ys[i * MS + c];
+                if (q == 0) {
+                    float *st = prm.carry_st + (size_t)slot * CARRY_W;
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        st[j] = p[j];
+                        st[16 + j] = pb[j];
+                    }
+                    st[32] = tau;
+                    st[33] = sigma;
+                    st[34] = __int_as_float(it_pt);
+                    prm.carry_list[slot] = pt;
+                }
+                __syncwarp(gmask);
+                fetch();
+            } else if (((wit + 1) % g) == 0) {
                 float dq = 1.f;
 #pragma unroll
                 for (int a = 0; a < NS; ++a) {
@@ -323,15 +397,16 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
 // Host launcher: picks the instantiation for (NS, m); TPP = 4.
 int small_supported_ns(int n) { return (n + 1) & ~1; }
 
-cudaError_t launch_pdhg_small(int NS, int m, int grid, int threads, size_t smem, cudaStream_t s,
+cudaError_t launch_pdhg_small(int NS, int m, int tpp, int grid, int threads, size_t smem, cudaStream_t s,
                               const float *inst, const SolveParams &prm, int ys_stride, const float *x,
                               const float *p_init, float *phi, float *pstar, float *gap, int *iters,
                               int *status, int *counter) {
     void (*fn)(const float *, SolveParams, int, const float *, const float *, float *, float *, float *,
                int *, int *, int *) = nullptr;
-#define HOPF_CASE(NSV)                                                                      \
-    case NSV:                                                                               \
-        fn = (m == 1) ? pdhg_small_kernel<NSV, 1, 4> : pdhg_small_kernel<NSV, 2, 4>;        \
+#define HOPF_CASE(NSV)                                                                           \
+    case NSV:                                                                                    \
+        if (tpp == 32) fn = (m == 1) ? pdhg_small_kernel<NSV, 1, 32> : pdhg_small_kernel<NSV, 2, 32>; \
+        else fn = (m == 1) ? pdhg_small_kernel<NSV, 1, 4> : pdhg_small_kernel<NSV, 2, 4>;        \
         break;
     switch (NS) {
         HOPF_CASE(2) HOPF_CASE(4) HOPF_CASE(6) HOPF_CASE(8)

@@ -23,9 +23,11 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                                        const double *__restrict__ Tv, const int *__restrict__ active,
                                        int n_inst, int n, int m, int N, int rule, double tau,
                                        double sigma_scale, double *out64, float *out32,
-                                       double *scratch) {
+                                       double *scratch, bool smem_scratch) {
     const InstanceLayout L = InstanceLayout::make(n, m, N);
-    double *sc = scratch + (long long)blockIdx.x * table_scratch_doubles(n, m);
+    // scratch in shared memory when the launch provides it (small n), else global
+    extern __shared__ double tsm[];
+    double *sc = smem_scratch ? tsm : scratch + (long long)blockIdx.x * table_scratch_doubles(n, m);
     double *X = sc, *T1 = X + n * n, *Eh = T1 + n * n, *ET = Eh + n * n, *T2 = ET + n * n;
     double *C = T2 + n * n, *Aug = C + n * n;             // Aug: 2 n^2
     double *Ga = Aug + 2 * n * n, *Gb = Ga + n * m;
@@ -91,10 +93,28 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         for (int e = threadIdx.x; e < n * n; e += blockDim.x)
             So[e] = okS ? T2[e] : __longlong_as_double(0x7ff8000000000000LL);
         __syncthreads();
-        double L2 = cta::lambda_max(C, n, v, u, red);
+        // |K|^2 = largest eigenvalue of the Gram matrix: Jacobi for small n
+        // (a few hundred block barriers), the power method otherwise
+        double L2;
+        if (n <= 64) {
+            cta::copy(X, C, n * n);
+            cta::sym_eig(X, T1, v, n, red);
+            if (threadIdx.x == 0) {
+                double mx = v[0];
+                for (int i = 1; i < n; ++i) mx = fmax(mx, v[i]);
+                red[6] = mx;
+            }
+            __syncthreads();
+            L2 = red[6];
+            __syncthreads();
+        } else {
+            L2 = cta::lambda_max(C, n, v, u, red);
+        }
         // M = U diag(lam) U^T for the accelerated prox (I + tau M/2)^-1 = U diag(1/(1 + tau lam/2)) U^T
         cta::copy(T2, Mo, n * n);
-        cta::sym_eig(T2, o + L.U, o + L.lam, n, red);
+        cta::sym_eig(T2, T1, v, n, red);
+        cta::copy(o + L.U, T1, n * n);
+        cta::copy(o + L.lam, v, n);
         if (threadIdx.x == 0) {
             double lmin = o[L.lam];
             for (int i = 1; i < n; ++i) lmin = fmin(lmin, o[L.lam + i]);
@@ -128,8 +148,10 @@ cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const 
                                    const double *qd, const double *W, const double *Tv, const int *active,
                                    int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
                                    double *out64, float *out32, double *scratch) {
-    build_instances_kernel<<<grid, threads, 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule, tau,
-                                                    sigma_scale, out64, out32, scratch);
+    const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
+    const bool in_smem = bytes <= 48 * 1024;
+    build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
+                                                                      tau, sigma_scale, out64, out32, scratch, in_smem);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from .api import HopfError, Options, _check, _Marshal
+from .api import Options, _check, _Marshal
 
 
 class WarmStartNet:
@@ -114,29 +114,27 @@ class WarmStartNet:
 
 
 def value_warm(system, x, t, net, opts=None, max_iter_warm=None, stream=None):
-    """Warm-started batched value solve (float32, device tensors).  Returns
-    dict(phi, p, gap, iters, status, n_fallback)."""
+    """Warm-started batched value solve (float32; device tensors, or numpy host
+    arrays copied in and out inside the call).  Returns dict(phi, p, gap,
+    iters, status, n_fallback)."""
     import torch
     lib = _lib.load()
     opts = opts or Options()
     mar = _Marshal(opts.precision, x)
-    if not mar.device:
-        raise HopfError("value_warm needs device tensors")
     xx = mar.inp(x)
     P = int(xx.shape[0])
     scalar_t = np.ndim(t) == 0 and not (hasattr(t, "ndim") and t.ndim > 0)
     tt = mar.inp(np.array([float(t)]) if scalar_t else t)
     out = dict(phi=mar.out((P,)), p=mar.out((P, system.n)), gap=mar.out((P,)),
                iters=mar.out((P,), True), status=mar.out((P,), True))
-    nfb = torch.zeros(1, dtype=torch.int32, device=xx.device)
+    nfb = torch.zeros(1, dtype=torch.int32, device=xx.device) if mar.device else np.zeros(1, np.int32)
     prob = system.c_struct()
-    o = opts.c_struct(False)
+    o = opts.c_struct(not mar.device)
     c = net.c_struct()
     mi = opts.max_iter if max_iter_warm is None else int(max_iter_warm)
     rc = lib.hopf_value_warm(ctypes.byref(prob), ctypes.byref(o), ctypes.byref(c), P, mar.ptr(xx), mar.ptr(tt),
                              0 if scalar_t else 1, mi, mar.ptr(out["phi"]), mar.ptr(out["p"]), mar.ptr(out["gap"]),
-                             mar.ptr(out["iters"]), mar.ptr(out["status"]), ctypes.c_void_p(nfb.data_ptr()),
-                             mar.stream(stream))
+                             mar.ptr(out["iters"]), mar.ptr(out["status"]), mar.ptr(nfb), mar.stream(stream))
     _check(lib, rc)
     out["n_fallback"] = nfb
     return out
