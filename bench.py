@@ -48,8 +48,8 @@ def rank_env():
 
 def workload(rank, points=POINTS):
     # rank r solves its own seeded points; rank 0 is the standard point set
-    w = wl.workload_random10(points, seed_sys=1, seed_pts=2 + 1000 * rank)
-    return w
+    from paper_1712_08226_gb300 import shard
+    return wl.workload_random10(points, seed_sys=1, seed_pts=shard.rank_point_seed(rank))
 
 
 def flops_per_point_iter(n, m, N):
@@ -306,18 +306,16 @@ def main():
     if not e2e_s:
         e2e_s = [float("nan")]
 
+    from paper_1712_08226_gb300 import shard
     mean_ms = statistics.mean(step_ms)
-    t_local = np.array([mean_ms, statistics.mean(e2e_s) * 1e3], dtype=np.float64)
+    t_local = shard.reduce_max([mean_ms, statistics.mean(e2e_s) * 1e3], dist, device="cuda" if dist else None)
     if dist:
-        tt = torch.tensor(t_local, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_local = tt.cpu().numpy()
         dist.destroy_process_group()
     if rank != 0:
         return
     solves_per_step = ok / args.steps
-    value = world * solves_per_step / (t_local[0] * 1e-3)
-    e2e_value = world * ok_e2e / (t_local[1] * 1e-3)
+    value = shard.job_throughput(solves_per_step, world, t_local[0] * 1e-3)
+    e2e_value = shard.job_throughput(ok_e2e, world, t_local[1] * 1e-3)
 
     fpi = flops_per_point_iter(n, m, N)
     achieved = units / args.steps * fpi / (statistics.mean(solve_ms) * 1e-3) / 1e12
