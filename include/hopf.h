@@ -107,11 +107,14 @@ typedef struct {
                            theta = 1/sqrt(1 + 2 gamma tau), tau *= theta,
                            sigma /= theta, pbar = p + theta (p - p_old).  The
                            starting tau is opts->tau.                             */
-    int park_iters;     /* small-state float32 solves run in two phases: 4 lanes
-                           per point, then points still uncertified after
-                           park_iters iterations continue with 32 lanes per
-                           point (lower latency for the slowest points).
-                           0 = library default (1024); < 0 = one phase only.      */
+    int park_iters;     /* small-state float32 solves run in up to three phases:
+                           4 lanes per point, 32 lanes per point, one thread
+                           block per point (less work per iteration first,
+                           lower latency per iteration later).  A point moves
+                           on after park_iters iterations in a phase (5x that
+                           in the second), or as soon as its phase has no new
+                           point left to start.  0 = library default (4096);
+                           < 0 = first phase only.                                */
 } hopf_opts;
 
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,

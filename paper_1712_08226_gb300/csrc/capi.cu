@@ -24,6 +24,9 @@ template <typename R>
 cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
                                 R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
                                 const int *active, cudaStream_t s);
+cudaError_t launch_pdhg_cta(int NS, int m, int grid, cudaStream_t s, const float *inst, const SolveParams &prm,
+                            const float *x, float *phi, float *pstar, float *gap, int *iters, int *status,
+                            int *counter);
 cudaError_t launch_pdhg_small(int NS, int m, int tpp, int grid, int threads, size_t smem, cudaStream_t s,
                               const float *inst, const SolveParams &prm, int ys_stride, const float *x,
                               const float *p_init, float *phi, float *pstar, float *gap, int *iters,
@@ -57,6 +60,51 @@ cudaError_t mlp_adam(long long count, float *w, __nv_bfloat16 *wb, const float *
                      float b1, float b2, float eps, int step, cudaStream_t s);
 cudaError_t mlp_sync_bf16(long long count, const float *w, __nv_bfloat16 *wb, cudaStream_t s);
 
+// Hardest-first order for the warm solve: points whose predicted p* is small
+// take the most iterations (the relative gap then asks for a small absolute
+// gap), so they are started first.  Buckets of |p_hat|^2 by powers of two,
+// ascending; order within a bucket unspecified.
+constexpr int ORDER_BUCKETS = 64;
+__global__ void order_count_kernel(int P, int n, const float *phat, int *bucket, int *counts) {
+    __shared__ int h[ORDER_BUCKETS];
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        float s = 0.f;
+        for (int j = 0; j < n; ++j) {
+            float v = phat[(long long)k * n + j];
+            s = fmaf(v, v, s);
+        }
+        int e = 0;
+        frexpf(s, &e);                         // s = f 2^e, f in [0.5, 1)
+        int b = s > 0.f ? e + 32 : 0;
+        b = b < 0 ? 0 : (b >= ORDER_BUCKETS ? ORDER_BUCKETS - 1 : b);
+        bucket[k] = b;
+        atomicAdd(&h[b], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], h[i]);
+}
+__global__ void order_scan_kernel(int P, int hard, int *counts, int *total) {
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int i = 0; i < ORDER_BUCKETS; ++i) {
+            int c = counts[i];
+            counts[i] = run;                   // exclusive prefix: cursor of bucket i
+            run += c;
+        }
+        total[0] = P;                          // whole list
+        total[1] = hard;                       // hardest points (latency kernel)
+        total[2] = P - hard;                   // the rest (throughput kernel)
+    }
+}
+__global__ void order_scatter_kernel(int P, const int *bucket, int *cursor, int *list) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) list[atomicAdd(&cursor[bucket[k]], 1)] = k;
+}
+
 // list of the points whose status is not OK (order unspecified)
 __global__ void failed_points_kernel(int P, const int *status, int *list, int *count) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,6 +124,7 @@ struct Workspace {
     size_t size = 0;
 };
 std::vector<Workspace> g_ws;
+
 
 // events of the last profiled hopf_value call
 struct Profile {
@@ -99,6 +148,26 @@ int fail(int code, const char *fmt, ...) {
         cudaError_t e_ = (call);                                                                \
         if (e_ != cudaSuccess) return fail(HOPF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
+
+// side stream and fork/join events per device (the warm solve runs its
+// hardest points concurrently with the rest)
+struct Side {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::vector<Side> g_side;
+
+int side_stream(int dev, Side **out) {
+    if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
+    Side &sd = g_side[dev];
+    if (!sd.stream) {
+        CU(cudaStreamCreateWithFlags(&sd.stream, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming));
+    }
+    *out = &sd;
+    return HOPF_SUCCESS;
+}
 
 // Bump allocator over the device workspace; a first pass with base == nullptr
 // only measures.
@@ -240,14 +309,14 @@ int upload_problem(const DevProblem &d, const hopf_problem *pr, cudaStream_t s) 
     return HOPF_SUCCESS;
 }
 
-int table_threads(int n) { return n >= 24 ? 256 : 64; }
+// one warp builds a small table (its block barriers are cheap); more threads for large n
+int table_threads(int n) { return n <= 16 ? 32 : (n <= 32 ? 64 : 256); }
 
 // ------------------------------------------------------------ small kernel
 constexpr int SMALL_MAX_THREADS = 384;
-// Two-phase solve: points not certified after this many iterations of the
-// throughput phase (4 lanes per point) are finished by the latency phase
-// (32 lanes per point).
-constexpr int SMALL_PARK_ITERS = 1024;
+// Multi-phase solve: a point moves on to the next (lower-latency) phase after
+// this many iterations, or as soon as its phase has no new point left.
+constexpr int SMALL_PARK_ITERS = 4096;
 
 struct SmallPlan {
     bool ok = false;
@@ -284,42 +353,67 @@ SmallPlan plan_small(const Device &dev, int n, int m, int N, int P, int tpp = 4)
 
 struct CarryBufs {
     float *y = nullptr, *st = nullptr;
-    int *list = nullptr, *count = nullptr, *ctr = nullptr;
+    int *list = nullptr, *count = nullptr;
+};
+struct CarryPair {
+    CarryBufs a, b;
+    int *ctr = nullptr;   // [3] point counters of the three phases
 };
 
 template <typename AR>
-CarryBufs take_carry(AR &a, int P, int N, int m) {
-    CarryBufs cb;
-    cb.y = a.template take<float>((size_t)P * N * m);
-    cb.st = a.template take<float>((size_t)P * CARRY_W);
-    cb.list = a.template take<int>(P);
-    cb.count = a.template take<int>(4);
-    cb.ctr = a.template take<int>(4);
-    return cb;
+CarryPair take_carry(AR &ar, int P, int N, int m) {
+    CarryPair cp;
+    for (CarryBufs *cb : {&cp.a, &cp.b}) {
+        cb->y = ar.template take<float>((size_t)P * N * m);
+        cb->st = ar.template take<float>((size_t)P * CARRY_W);
+        cb->list = ar.template take<int>(P);
+        cb->count = ar.template take<int>(4);
+    }
+    cp.ctr = ar.template take<int>(4);
+    return cp;
 }
 
-// Throughput phase (4 lanes per point) that parks slow points, then the
-// latency phase (32 lanes per point) that finishes them.
+// Small-state float32 solve in up to three phases:
+//   1. 4 lanes per point (throughput); points uncertified after park_iters
+//      iterations are parked;
+//   2. 32 lanes per point resumes them; points still uncertified after
+//      4 park_iters more are parked again;
+//   3. one 256-thread block per point (latency) finishes the rest.
 int run_small_two_phase(const SmallPlan &sp, const SmallPlan &sp32, int m, const float *inst, SolveParams prm,
                         const float *x, const float *pinit, float *phi, float *pstar, float *gap, int *iters,
-                        int *status, const CarryBufs &cb, int park_iters, cudaStream_t s) {
-    CU(cudaMemsetAsync(cb.ctr, 0, sizeof(int), s));
-    CU(cudaMemsetAsync(cb.count, 0, sizeof(int), s));
-    const bool two = sp32.ok && park_iters >= 0;
-    prm.carry_cap = two ? (park_iters > 0 ? park_iters : SMALL_PARK_ITERS) : 0;
+                        int *status, const CarryPair &cp, int park_iters, cudaStream_t s) {
+    CU(cudaMemsetAsync(cp.ctr, 0, 3 * sizeof(int), s));
+    CU(cudaMemsetAsync(cp.a.count, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(cp.b.count, 0, sizeof(int), s));
+    const bool multi = sp32.ok && park_iters >= 0 && prm.N <= 512;
+    const int cap = park_iters > 0 ? park_iters : SMALL_PARK_ITERS;
+    prm.carry_cap = multi ? cap : 0;
     prm.carry_in = 0;
-    prm.carry_y = cb.y;
-    prm.carry_st = cb.st;
-    prm.carry_list = cb.list;
-    prm.carry_count = cb.count;
+    prm.out_y = cp.a.y;
+    prm.out_st = cp.a.st;
+    prm.out_list = cp.a.list;
+    prm.out_count = cp.a.count;
     CU(launch_pdhg_small(sp.NS, m, sp.tpp, sp.grid, sp.threads, sp.smem, s, inst, prm, sp.ys_stride, x, pinit, phi,
-                         pstar, gap, iters, status, cb.ctr));
-    if (!two) return HOPF_SUCCESS;
-    CU(cudaMemsetAsync(cb.ctr + 1, 0, sizeof(int), s));
-    prm.carry_cap = 0;
+                         pstar, gap, iters, status, cp.ctr));
+    if (!multi) return HOPF_SUCCESS;
     prm.carry_in = 1;
+    prm.in_y = cp.a.y;
+    prm.in_st = cp.a.st;
+    prm.in_list = cp.a.list;
+    prm.in_count = cp.a.count;
+    prm.carry_cap = 5 * cap;
+    prm.out_y = cp.b.y;
+    prm.out_st = cp.b.st;
+    prm.out_list = cp.b.list;
+    prm.out_count = cp.b.count;
     CU(launch_pdhg_small(sp32.NS, m, sp32.tpp, sp32.grid, sp32.threads, sp32.smem, s, inst, prm, sp32.ys_stride, x,
-                         pinit, phi, pstar, gap, iters, status, cb.ctr + 1));
+                         pinit, phi, pstar, gap, iters, status, cp.ctr + 1));
+    prm.carry_cap = 0;
+    prm.in_y = cp.b.y;
+    prm.in_st = cp.b.st;
+    prm.in_list = cp.b.list;
+    prm.in_count = cp.b.count;
+    CU(launch_pdhg_cta(sp.NS, m, 2 * sp32.grid, s, inst, prm, x, phi, pstar, gap, iters, status, cp.ctr + 2));
     return HOPF_SUCCESS;
 }
 
@@ -379,7 +473,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     }
     const int tgrid = table_grid(dev, n_inst);
     const bool hio = o->host_io != 0;
-    CarryBufs cb;
+    CarryPair cb;
 
     auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
                     R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
@@ -665,8 +759,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     DevProblem d;
     double *Tv, *i64, *tsc;
     float *i32, *phat, *msc, *y;
-    int *list, *cnt, *ctr;
-    CarryBufs cb;
+    int *list, *cnt, *ctr, *ord, *obucket, *ocount, *ototal;
+    CarryPair cb;
     const bool hio = o->host_io != 0;
     float *dx, *dt, *dphi, *dps, *dgap;
     int *dit, *dst;
@@ -688,6 +782,10 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         list = a.template take<int>(P);
         cnt = a.template take<int>(4);
         ctr = a.template take<int>(4);
+        ord = a.template take<int>(P);
+        obucket = a.template take<int>(P);
+        ocount = a.template take<int>(ORDER_BUCKETS);
+        ototal = a.template take<int>(4);
         y = sp.ok ? nullptr : a.template take<float>((size_t)P * N * m);
         if (sp.ok) cb = take_carry(a, P, N, m);
     };
@@ -731,12 +829,47 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
                                        o->park_iters, s);
         return launch_generic<float>(i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
     };
+    // hardest-first order of the warm solve; the hardest points (one wave of
+    // the 32-lane kernel on a quarter of the SMs) run concurrently with the rest
+    const bool split = false;
+    const int g_hard = split ? std::max(1, dev.sms / 4) : 0;
+    const int n_hard = split ? std::min(P, g_hard * sp32.pts) : 0;
+    CU(cudaMemsetAsync(ocount, 0, sizeof(int) * ORDER_BUCKETS, s));
+    order_count_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, n, phat, obucket, ocount);
+    order_scan_kernel<<<1, 32, 0, s>>>(P, n_hard, ocount, ototal);
+    order_scatter_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, obucket, ocount, ord);
+    CU(cudaGetLastError());
     // warm solve, capped at max_iter_warm
     SolveParams pw = prm;
     pw.warm = 1;
     pw.max_iter = max_iter_warm;
-    rc = solve(pw, phat);
-    if (rc) return rc;
+    pw.list = ord;
+    pw.list_count = ototal;
+    if (split) {
+        Side *sd = nullptr;
+        rc = side_stream(dev.id, &sd);
+        if (rc) return rc;
+        CU(cudaMemsetAsync(ctr + 1, 0, sizeof(int), s));
+        CU(cudaEventRecord(sd->fork, s));
+        CU(cudaStreamWaitEvent(sd->stream, sd->fork, 0));
+        SolveParams ph = pw;                       // hardest points, 32 lanes each
+        ph.list_count = ototal + 1;
+        ph.carry_cap = 0;
+        CU(launch_pdhg_small(sp32.NS, m, 32, g_hard, sp32.threads, sp32.smem, sd->stream, i32, ph, sp32.ys_stride,
+                             dx, phat, dphi, dps, dgap, dit, dst, ctr + 1));
+        SolveParams pe = pw;                       // the rest, 4 lanes each, parking slow ones
+        pe.list = ord + n_hard;
+        pe.list_count = ototal + 2;
+        SmallPlan spe = sp;
+        spe.grid = std::max(1, dev.sms - g_hard);
+        rc = run_small_two_phase(spe, sp32, m, i32, pe, dx, phat, dphi, dps, dgap, dit, dst, cb, o->park_iters, s);
+        if (rc) return rc;
+        CU(cudaEventRecord(sd->join, sd->stream));
+        CU(cudaStreamWaitEvent(s, sd->join, 0));
+    } else {
+        rc = solve(pw, phat);
+        if (rc) return rc;
+    }
     // cold fallback for every point that the warm solve did not certify
     CU(cudaMemsetAsync(cnt, 0, sizeof(int), s));
     failed_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dst, list, cnt);

@@ -50,15 +50,15 @@ struct SolveParams {
     int accel;         // Chambolle-Pock accelerated variant (strongly convex G)
     const int *list;        // optional: solve only the points list[0 .. *list_count)
     const int *list_count;  // device count for `list`
-    // two-phase solve of the small kernel: the throughput phase parks every
-    // point still uncertified after carry_cap iterations (carry_cap > 0); the
-    // latency phase (carry_in = 1) resumes the parked points
+    // multi-phase solve of the small-state kernels: a phase parks every point
+    // still uncertified after carry_cap iterations (carry_cap > 0) into the
+    // out_* buffers; a later phase (carry_in = 1) resumes the in_* points
     int carry_cap;
     int carry_in;
-    float *carry_y;         // [slot][N m] parked dual variables
-    float *carry_st;        // [slot][CARRY_W] p, pbar, tau, sigma, iteration count
-    int *carry_list;        // point index of each slot
-    int *carry_count;       // number of parked points
+    float *in_y, *out_y;      // [slot][N m] parked dual variables
+    float *in_st, *out_st;    // [slot][CARRY_W] p, pbar, tau, sigma, iteration count
+    int *in_list, *out_list;  // point index of each slot
+    int *in_count, *out_count;
     double tau, tol_gap, sign_floor;
 };
 

@@ -171,7 +171,7 @@ int run(const hopf_problem *pr, const hopf_opts *o, int P, const void *x, const 
         cudaMemcpyAsync(W, pr->W, sizeof(double) * n * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return HOPF_ECUDA;
     if (launch_horizons(n_inst, s, t, fp32, Tv) != cudaSuccess) return HOPF_ECUDA;
-    if (launch_build_instances(tgrid, n >= 24 ? 256 : 64, s, A, B, q, W, Tv, nullptr, n_inst, n, m, N, o->rule,
+    if (launch_build_instances(tgrid, n <= 16 ? 32 : (n <= 32 ? 64 : 256), s, A, B, q, W, Tv, nullptr, n_inst, n, m, N, o->rule,
                                o->tau, o->sigma_scale, i64, i32, tsc) != cudaSuccess)
         return HOPF_ECUDA;
     SolveParams prm{};

@@ -152,7 +152,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
     bool idle = false, have_D = false, fresh = false;
     float Dprev = 0.f;
     float tau = tau0, sigma = sigma0;      // current steps (they change only when accelerated)
-    const int n_carry = prm.carry_in ? *prm.carry_count : 0;
+    const int n_carry = prm.carry_in ? *prm.in_count : 0;
 
     // take the next point for this group; T = 0 points finish on the spot
     auto fetch = [&]() {
@@ -162,7 +162,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             nx = __shfl_sync(gmask, nx, lead);
             if (nx >= (prm.carry_in ? n_carry : P)) { idle = true; pt = -1; return; }
             slot_in = nx;
-            pt = prm.carry_in ? prm.carry_list[nx] : (prm.list ? prm.list[nx] : nx);
+            pt = prm.carry_in ? prm.in_list[nx] : (prm.list ? prm.list[nx] : nx);
             __syncwarp(gmask);
             if (q == 0) {
 #pragma unroll
@@ -188,7 +188,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
         if (prm.carry_in) {
             // resume a point parked by the throughput phase: primal state, step
             // sizes, iteration count and the dual variable y
-            const float *st = prm.carry_st + (size_t)slot_in * CARRY_W;
+            const float *st = prm.in_st + (size_t)slot_in * CARRY_W;
 #pragma unroll
             for (int j = 0; j < NS; ++j) {
                 p[j] = st[j];
@@ -197,7 +197,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             tau = st[32];
             sigma = st[33];
             it_pt = __float_as_int(st[34]);
-            const float *cy = prm.carry_y + (size_t)slot_in * N * MS;
+            const float *cy = prm.in_y + (size_t)slot_in * N * MS;
             for (int i = q; i < N; i += TPP)
 #pragma unroll
                 for (int c = 0; c < MS; ++c) ys[i * MS + c] = cy[(size_t)i * MS + c];
@@ -286,8 +286,12 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                         status[pt] = bad ? HOPF_NONFINITE : (conv ? HOPF_OK : HOPF_MAXITER);
                     }
                     fetch();
-                } else if (prm.carry_cap > 0 && it_pt - 1 >= prm.carry_cap) {
-                    park = true;       // hand over to the latency phase after this step
+                } else if (prm.carry_cap > 0 &&
+                           (it_pt - 1 >= prm.carry_cap || __ldcg(counter) >= (prm.carry_in ? n_carry : P))) {
+                    // hand over to the next (lower-latency) phase after this step: after
+                    // carry_cap iterations, or as soon as no new point is left to take
+                    // (then the slots of this phase would only drain)
+                    park = true;
                 }
             }
             if (__all_sync(0xffffffffu, idle)) break;
@@ -357,14 +361,14 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
             if (park) {
                 // save the point after this full step and take a new one
                 int slot = 0;
-                if (q == 0) slot = atomicAdd(prm.carry_count, 1);
+                if (q == 0) slot = atomicAdd(prm.out_count, 1);
                 slot = __shfl_sync(gmask, slot, lead);
-                float *cy = prm.carry_y + (size_t)slot * N * MS;
+                float *cy = prm.out_y + (size_t)slot * N * MS;
                 for (int i = q; i < N; i += TPP)
 #pragma unroll
                     for (int c = 0; c < MS; ++c) cy[(size_t)i * MS + c] = ys[i * MS + c];
                 if (q == 0) {
-                    float *st = prm.carry_st + (size_t)slot * CARRY_W;
+                    float *st = prm.out_st + (size_t)slot * CARRY_W;
 #pragma unroll
                     for (int j = 0; j < NS; ++j) {
                         st[j] = p[j];
@@ -373,7 +377,7 @@ pdhg_small_kernel(const float *__restrict__ inst, SolveParams prm, int ys_stride
                     st[32] = tau;
                     st[33] = sigma;
                     st[34] = __int_as_float(it_pt);
-                    prm.carry_list[slot] = pt;
+                    prm.out_list[slot] = pt;
                 }
                 __syncwarp(gmask);
                 fetch();

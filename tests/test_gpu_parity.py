@@ -276,3 +276,21 @@ def test_random10_accelerated_fp64(H):
     r = H.value(sysd, cuda(w["x"], torch.float64), w["t"], opts)
     assert np.all(r["status"].cpu().numpy() == 0)
     assert rel_err(np_(r["phi"]), np.array(g["phi"][:P])).max() <= 2e-9
+
+
+@pytest.mark.parametrize("accel", [False, True])
+def test_random10_parking_through_all_phases(H, accel):
+    # a tiny park threshold sends most points through the 32-lane phase and
+    # the block-per-point phase; results must not depend on where a point
+    # finished
+    g = gold("random10_values.json")
+    P = 320
+    w = wl.workload_random10(P)
+    sysd = H.System.from_dict(w["system"])
+    opts = H.Options(N=w["N"], tau=2.0 if accel else w["tau"], tol_gap=1e-5, accel=accel, park_iters=16)
+    r = H.value(sysd, cuda(w["x"]), w["t"], opts)
+    st = r["status"].cpu().numpy()
+    assert np.all(st == 0), np.unique(st, return_counts=True)
+    err = rel_err(np_(r["phi"]), np.array(g["phi"]))
+    assert err.max() <= 1e-5, err.max()
+    assert (r["iters"].cpu().numpy() > 16 * 6).sum() > 10          # some finished in the last phase
