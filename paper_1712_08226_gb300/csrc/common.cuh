@@ -64,7 +64,7 @@ struct SolveParams {
 
 // float64 scratch (elements) one thread block needs to build one instance
 __host__ __device__ inline long long table_scratch_doubles(int n, int m) {
-    return 9LL * n * n + 2LL * n * m + 2LL * n + 16;
+    return 9LL * n * n + 2LL * n * m + 8LL * n + 32;
 }
 
 constexpr int CARRY_W = 40;   // p [16], pbar [16], tau, sigma, iteration count, pad

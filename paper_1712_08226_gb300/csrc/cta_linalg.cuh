@@ -176,71 +176,96 @@ __device__ inline double lambda_max(const double *C, int n, double *v, double *u
     return lam;
 }
 
-// Eigen-decomposition of a symmetric matrix by cyclic Jacobi rotations
-// (Jacobi 1846; each rotation in the (p, q) plane annihilates a_pq:
-// theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
-// c = 1/sqrt(t^2 + 1), s = t c).  A (n x n, destroyed) becomes diagonal;
-// U (n x n) collects the rotations so that A_in = U diag(lam) U^T.
-__device__ inline void sym_eig(double *A, double *U, double *lam, int n, double *red) {
+// Eigen-decomposition of a symmetric matrix by Jacobi rotations (Jacobi
+// 1846) in the parallel round-robin order of Brent and Luk (1985): each round
+// pairs the indices into disjoint planes (p, q) (circle method), every pair's
+// rotation is computed from the same matrix, then all column rotations and
+// all row rotations are applied at once (disjoint planes commute).  The
+// rotation of plane (p, q) annihilates a_pq: theta = (a_qq - a_pp)/(2 a_pq),
+// t = sgn(theta)/(|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(t^2 + 1), s = t c,
+// and the 2 x 2 block becomes diag(a_pp - t a_pq, a_qq + t a_pq).
+// A (n x n, destroyed) becomes diagonal; U collects the rotations so that
+// A_in = U diag(lam) U^T.  rot: scratch of 6 * ceil(n/2) + 2 doubles.
+__device__ inline void sym_eig(double *A, double *U, double *lam, int n, double *red, double *rot) {
     set_identity(U, n);
+    const int ne = n + (n & 1), half = ne / 2;
     for (int sweep = 0; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) {
-            double off = 0.0, tot = 0.0;
-            for (int i = 0; i < n; ++i)
-                for (int j = 0; j < n; ++j) {
-                    double v = A[i * n + j] * A[i * n + j];
-                    tot += v;
-                    if (i != j) off += v;
-                }
-            red[0] = off;
-            red[1] = tot;
-        }
+        if (threadIdx.x == 0) { red[0] = 0.0; red[1] = 0.0; }
         __syncthreads();
-        bool done = !(red[0] > 1e-30 * red[1]);
+        double off = 0.0, tot = 0.0;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            double v = A[e] * A[e];
+            tot += v;
+            if (e / n != e % n) off += v;
+        }
+        atomicAdd(&red[0], off);
+        atomicAdd(&red[1], tot);
+        __syncthreads();
+        const bool done = !(red[0] > 1e-30 * red[1]);
         __syncthreads();
         if (done) break;
-        for (int p = 0; p < n - 1; ++p) {
-            for (int q = p + 1; q < n; ++q) {
-                if (threadIdx.x == 0) {
-                    double apq = A[p * n + q];
-                    double c = 1.0, s = 0.0, t = 0.0;
+        for (int r = 0; r < ne - 1; ++r) {
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int a = k == 0 ? r : (r + k) % (ne - 1);
+                int b = k == 0 ? ne - 1 : (r - k + (ne - 1)) % (ne - 1);
+                int p = a < b ? a : b, q = a < b ? b : a;
+                double *R = rot + 6 * k;
+                R[0] = 1.0; R[1] = 0.0; R[2] = 0.0; R[3] = 0.0;
+                if (q < n) {
+                    const double apq = A[p * n + q];
+                    R[4] = A[p * n + p];
+                    R[5] = A[q * n + q];
                     if (apq != 0.0) {
-                        double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                        t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
-                    }
-                    red[2] = c;
-                    red[3] = s;
-                    red[4] = t;
-                    red[5] = apq;
-                }
-                __syncthreads();
-                const double c = red[2], s = red[3], t = red[4], apq = red[5];
-                if (apq != 0.0) {
-                    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                        if (k != p && k != q) {
-                            double akp = A[k * n + p], akq = A[k * n + q];
-                            double np_ = c * akp - s * akq, nq_ = s * akp + c * akq;
-                            A[k * n + p] = np_;
-                            A[p * n + k] = np_;
-                            A[k * n + q] = nq_;
-                            A[q * n + k] = nq_;
-                        }
-                        double ukp = U[k * n + p], ukq = U[k * n + q];
-                        U[k * n + p] = c * ukp - s * ukq;
-                        U[k * n + q] = s * ukp + c * ukq;
-                    }
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        A[p * n + p] -= t * apq;
-                        A[q * n + q] += t * apq;
-                        A[p * n + q] = 0.0;
-                        A[q * n + p] = 0.0;
+                        double th = (R[5] - R[4]) / (2.0 * apq);
+                        double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        double c = 1.0 / sqrt(t * t + 1.0);
+                        R[0] = c; R[1] = t * c; R[2] = t; R[3] = apq;
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            // column rotations (A and U), then row rotations, then the 2 x 2 blocks
+            for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+                int k = e / n, i = e % n;
+                int a = k == 0 ? r : (r + k) % (ne - 1);
+                int b = k == 0 ? ne - 1 : (r - k + (ne - 1)) % (ne - 1);
+                int p = a < b ? a : b, q = a < b ? b : a;
+                const double *R = rot + 6 * k;
+                if (q >= n || R[3] == 0.0) continue;
+                double c = R[0], sn = R[1];
+                double ap = A[i * n + p], aq = A[i * n + q];
+                A[i * n + p] = c * ap - sn * aq;
+                A[i * n + q] = sn * ap + c * aq;
+                double up = U[i * n + p], uq = U[i * n + q];
+                U[i * n + p] = c * up - sn * uq;
+                U[i * n + q] = sn * up + c * uq;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+                int k = e / n, j = e % n;
+                int a = k == 0 ? r : (r + k) % (ne - 1);
+                int b = k == 0 ? ne - 1 : (r - k + (ne - 1)) % (ne - 1);
+                int p = a < b ? a : b, q = a < b ? b : a;
+                const double *R = rot + 6 * k;
+                if (q >= n || R[3] == 0.0) continue;
+                double c = R[0], sn = R[1];
+                double ap = A[p * n + j], aq = A[q * n + j];
+                A[p * n + j] = c * ap - sn * aq;
+                A[q * n + j] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int a = k == 0 ? r : (r + k) % (ne - 1);
+                int b = k == 0 ? ne - 1 : (r - k + (ne - 1)) % (ne - 1);
+                int p = a < b ? a : b, q = a < b ? b : a;
+                const double *R = rot + 6 * k;
+                if (q >= n || R[3] == 0.0) continue;
+                A[p * n + p] = R[4] - R[2] * R[3];
+                A[q * n + q] = R[5] + R[2] * R[3];
+                A[p * n + q] = 0.0;
+                A[q * n + p] = 0.0;
+            }
+            __syncthreads();
         }
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = A[i * n + i];

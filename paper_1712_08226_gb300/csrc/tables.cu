@@ -33,7 +33,8 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
     double *Ga = Aug + 2 * n * n, *Gb = Ga + n * m;
     double *v = Gb + n * m, *u = v + n;
     double *red = u + n;                                  // 8 doubles
-    int *piv = (int *)(red + 8);
+    double *rot = red + 8;                                // 3n + 8 doubles (Jacobi rotations)
+    int *piv = (int *)(rot + 3 * n + 8);
 
     for (int inst = blockIdx.x; inst < n_inst; inst += gridDim.x) {
         if (active && !active[inst]) continue;
@@ -98,7 +99,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         double L2;
         if (n <= 64) {
             cta::copy(X, C, n * n);
-            cta::sym_eig(X, T1, v, n, red);
+            cta::sym_eig(X, T1, v, n, red, rot);
             if (threadIdx.x == 0) {
                 double mx = v[0];
                 for (int i = 1; i < n; ++i) mx = fmax(mx, v[i]);
@@ -112,7 +113,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         }
         // M = U diag(lam) U^T for the accelerated prox (I + tau M/2)^-1 = U diag(1/(1 + tau lam/2)) U^T
         cta::copy(T2, Mo, n * n);
-        cta::sym_eig(T2, T1, v, n, red);
+        cta::sym_eig(T2, T1, v, n, red, rot);
         cta::copy(o + L.U, T1, n * n);
         cta::copy(o + L.lam, v, n);
         if (threadIdx.x == 0) {
