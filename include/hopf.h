@@ -255,6 +255,16 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
                     int *n_fallback, void *stream);
 
 /*
+ * hopf_tc_selftest - diagnostic of the tensor-core primitives used by the
+ * large-state kernels (no counterpart in the paper).  One thread block
+ * computes D[128][N] = A[128][K] B[N][K]^T with tcgen05.mma of kind::tf32
+ * (float32 accumulation in tensor memory) and writes D.  Device arrays,
+ * row-major; 16 <= N <= 256 (multiple of 16), 8 <= K <= 128 (multiple of 8).
+ * *err (device int) is set to 1 if the completion wait timed out.
+ */
+int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int *err, void *stream);
+
+/*
  * hopf_value_noalloc - hopf_value for callers that cannot allocate memory.
  *
  * The paper has no counterpart; this is a deployment variant.  Some callers

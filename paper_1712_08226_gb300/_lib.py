@@ -31,7 +31,7 @@ class HopfMlp(ctypes.Structure):
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",
            "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile",
            "hopf_value_noalloc", "hopf_mlp_param_count", "hopf_mlp_sync", "hopf_mlp_forward",
-           "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm")
+           "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm", "hopf_tc_selftest")
 
 _lib = None
 
@@ -81,5 +81,7 @@ def load(path=LIB_PATH):
     lib.hopf_value_warm.argtypes = [PP, PO, PM, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p,
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.hopf_value_warm.restype = c_int
+    lib.hopf_tc_selftest.argtypes = [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hopf_tc_selftest.restype = c_int
     _lib = lib
     return lib

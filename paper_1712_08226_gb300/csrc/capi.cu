@@ -24,6 +24,7 @@ template <typename R>
 cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
                                 R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
                                 const int *active, cudaStream_t s);
+cudaError_t launch_tc_selftest(int N, int K, const float *A, const float *B, float *D, int *err, cudaStream_t s);
 cudaError_t launch_pdhg_cta(int NS, int m, int grid, cudaStream_t s, const float *inst, const SolveParams &prm,
                             const float *x, float *phi, float *pstar, float *gap, int *iters, int *status,
                             int *counter);
@@ -1043,6 +1044,15 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
     if (!x || !t || !phi || !p_star || !gap || !iters || !status) return fail(HOPF_EINVAL, "null array");
     return value_warm_impl(prob, opts, net, P, x, t, t_stride, max_iter_warm, phi, p_star, gap, iters, status,
                            n_fallback, (cudaStream_t)stream);
+}
+
+int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int *err, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (N < 16 || N > 256 || N % 16 || K < 8 || K > 128 || K % 8 || !A || !B || !D || !err)
+        return fail(HOPF_EINVAL, "self-test sizes: 16 <= N <= 256 (multiple of 16), 8 <= K <= 128 (multiple of 8)");
+    CU(launch_tc_selftest(N, K, A, B, D, err, (cudaStream_t)stream));
+    return HOPF_SUCCESS;
 }
 
 const char *hopf_status_string(int code) {
