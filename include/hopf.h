@@ -216,6 +216,12 @@ typedef struct {
     float *adam_m, *adam_v;   /* optimiser moments (training only; may be NULL)     */
     const float *x_shift, *x_scale;   /* [n_in]  */
     const float *y_shift, *y_scale;   /* [n_out] */
+    int use_tc;               /* prediction (hopf_mlp_forward, hopf_value_warm) on
+                                 the tensor cores: tcgen05 MMA with bfloat16
+                                 activations and weights, float32 accumulation
+                                 (hidden, n_out <= 256); 0: float32 CUDA-core
+                                 products with bfloat16 weights.  Training
+                                 (hopf_mlp_loss_grad) always uses the latter.    */
 } hopf_mlp;
 
 /* Number of parameters of the network (weights and biases). */

@@ -25,7 +25,7 @@ class HopfOpts(ctypes.Structure):
 class HopfMlp(ctypes.Structure):
     _fields_ = [("n_in", c_int), ("hidden", c_int), ("n_out", c_int), ("w", c_void_p), ("w_bf16", c_void_p),
                 ("adam_m", c_void_p), ("adam_v", c_void_p), ("x_shift", c_void_p), ("x_scale", c_void_p),
-                ("y_shift", c_void_p), ("y_scale", c_void_p)]
+                ("y_shift", c_void_p), ("y_scale", c_void_p), ("use_tc", c_int)]
 
 
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",

@@ -54,6 +54,9 @@ long long mlp_scratch_floats(int n_in, int h, int n_out, int B, bool train);
 cudaError_t mlp_forward(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,
                         const float *x_scale, const float *y_shift, const float *y_scale, int B, const float *x,
                         float *y, float *scratch, bool keep_pre, cudaStream_t s);
+cudaError_t mlp_forward_tc(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w,
+                           const float *x_shift, const float *x_scale, const float *y_shift, const float *y_scale,
+                           int B, const float *x, float *y, float *scratch, int *err, cudaStream_t s);
 cudaError_t mlp_loss_grad(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,
                           const float *x_scale, const float *y_shift, const float *y_scale, int B, const float *x,
                           const float *y, float *loss, float *grad, float *scratch, cudaStream_t s);
@@ -732,6 +735,18 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     return HOPF_SUCCESS;
 }
 
+// network prediction: tensor cores when requested and the layers fit one MMA in N
+int net_predict(const hopf_mlp *net, int B, const float *x, float *y, float *scratch, int *err, cudaStream_t s) {
+    if (net->use_tc && net->hidden <= 256 && net->n_out <= 256) {
+        CU(mlp_forward_tc(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
+                          net->x_scale, net->y_shift, net->y_scale, B, x, y, scratch, err, s));
+    } else {
+        CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
+                       net->x_scale, net->y_shift, net->y_scale, B, x, y, scratch, false, s));
+    }
+    return HOPF_SUCCESS;
+}
+
 int check_mlp(const hopf_mlp *net) {
     if (!net) return fail(HOPF_EINVAL, "null network");
     if (net->n_in < 1 || net->hidden < 1 || net->n_out < 1 || net->hidden > 65536)
@@ -818,8 +833,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
     if (rc) return rc;
     // prediction of p* from x
-    CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
-                   net->x_scale, net->y_shift, net->y_scale, P, dx, phat, msc, false, s));
+    rc = net_predict(net, P, dx, phat, msc, ctr + 3, s);
+    if (rc) return rc;
     if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     SolveParams prm;
     fill_params(prm, pr, o, P);
@@ -990,12 +1005,11 @@ int hopf_mlp_forward(const hopf_mlp *net, int B, const float *x, float *y, void 
     if (B < 0 || (B > 0 && (!x || !y))) return fail(HOPF_EINVAL, "bad batch or null array");
     if (B == 0) return HOPF_SUCCESS;
     void *base = nullptr;
-    rc = ensure_workspace(sizeof(float) * (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, false),
-                          &base);
+    const size_t fl = (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, false);
+    rc = ensure_workspace(sizeof(float) * fl + 256, &base);
     if (rc) return rc;
-    CU(mlp_forward(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
-                   net->x_scale, net->y_shift, net->y_scale, B, x, y, (float *)base, false, (cudaStream_t)stream));
-    return HOPF_SUCCESS;
+    int *err = (int *)((char *)base + ((sizeof(float) * fl + 127) & ~(size_t)127));
+    return net_predict(net, B, x, y, (float *)base, err, (cudaStream_t)stream);
 }
 
 int hopf_mlp_loss_grad(const hopf_mlp *net, int B, const float *x, const float *y, float *loss, float *grad,

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace hopf {
 
@@ -208,6 +209,98 @@ __global__ void to_bf16_kernel(long long count, const float *w, __nv_bfloat16 *w
     if (e < count) wb[e] = __float2bfloat16_rn(w[e]);
 }
 
+// C[M x N] = A[M x K] W[N x K]^T on the tensor cores (tcgen05.mma, kind::f16):
+// A (float32 activations) and W (bfloat16 weights) are staged in shared memory
+// as bfloat16, in K chunks of 64, in the core-matrix layout of tc.cuh; the
+// float32 accumulator (128 rows x up to 256 columns) lives in tensor memory
+// and the epilogue functor writes the result.  One 128-thread block per 128
+// rows (thread t owns row t, i.e. tensor-memory lane t); N <= 256.
+constexpr int TC_KC = 64;
+
+template <class Epi>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
+                                                      const __nv_bfloat16 *__restrict__ W, int ldw, Epi epi,
+                                                      int *err) {
+    extern __shared__ __align__(1024) unsigned char gsm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_taddr;
+    const int Np = (N + 15) & ~15;
+    constexpr int KB = TC_KC * 2;                 // bytes per staged row
+    unsigned char *As = gsm, *Ws = gsm + 128 * KB;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row0 = blockIdx.x * 128;
+    if (warp == 0) tc::tmem_alloc(&s_taddr, 256);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = s_taddr;
+    const uint32_t idesc = tc::make_idesc(128, Np, tc::FMT_BF16);
+    const int nchunks = (K + TC_KC - 1) / TC_KC;
+    int ok = 1;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+        const int k0 = ch * TC_KC;
+        for (int e = tid; e < 128 * TC_KC; e += 128) {
+            const int r = e / TC_KC, k = e % TC_KC;
+            const int gr = row0 + r, gk = k0 + k;
+            const float v = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(As + tc::core_offset(r, k, KB, 2)) = __float2bfloat16_rn(v);
+        }
+        for (int e = tid; e < Np * TC_KC; e += 128) {
+            const int r = e / TC_KC, k = e % TC_KC;
+            const int gk = k0 + k;
+            const __nv_bfloat16 v = (r < N && gk < K) ? W[(size_t)r * ldw + gk] : __float2bfloat16_rn(0.f);
+            *reinterpret_cast<__nv_bfloat16 *>(Ws + tc::core_offset(r, k, KB, 2)) = v;
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Ws);
+            const uint32_t sbo = (uint32_t)(KB / 16) * 128u;
+#pragma unroll
+            for (int kc = 0; kc < TC_KC / 16; ++kc)
+                tc::mma_bf16(taddr, tc::make_desc(a0 + 2u * kc * 128u, 128u, sbo),
+                             tc::make_desc(b0 + 2u * kc * 128u, 128u, sbo), idesc, (ch > 0 || kc > 0) ? 1u : 0u);
+            tc::mma_commit(&mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&mbar, (uint32_t)(ch & 1)) ? 1 : 0);
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        tc::mbar_wait(&mbar, (uint32_t)((nchunks - 1) & 1));   // second bounded chance for work in flight
+    }
+    tc::fence_after_sync();
+    if (ok) {
+        const int row = row0 + tid;
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row < M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < N) epi(row, c0 + i, v[i]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+}
+
+template <class Epi>
+cudaError_t gemm_tc(int M, int N, int K, const float *A, int lda, const __nv_bfloat16 *W, int ldw, Epi epi, int *err,
+                    cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    // 100 KB of dynamic shared memory keeps at most two blocks (2 x 256 tensor-memory columns) per SM
+    const size_t smem = 100 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gemm_tc_kernel<Epi><<<(M + 127) / 128, 128, smem, s>>>(M, N, K, A, lda, W, ldw, epi, err);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ host drivers
 long long mlp_param_count(int n_in, int h, int n_out) { return MlpDims{n_in, h, n_out}.count(); }
 
@@ -216,6 +309,22 @@ long long mlp_scratch_floats(int n_in, int h, int n_out, int B, bool train) {
     long long f = (long long)B * (n_in + 4LL * h + n_out);
     if (train) f += (long long)B * (2LL * h + n_out) + 8;
     return f;
+}
+
+cudaError_t mlp_forward_tc(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w,
+                           const float *x_shift, const float *x_scale, const float *y_shift, const float *y_scale,
+                           int B, const float *x, float *y, float *scratch, int *err, cudaStream_t s) {
+    MlpDims d{n_in, h, n_out};
+    float *h0 = scratch, *h1 = h0 + (long long)B * n_in + (long long)B * h, *h2 = h1 + (long long)B * h + (long long)B * h;
+    long long tot = (long long)B * n_in;
+    standardize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, n_in, x, x_shift, x_scale, h0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = gemm_tc(B, h, n_in, h0, n_in, wb + d.oW1(), n_in, EpiBiasGelu{w + d.ob1(), nullptr, h1, h}, err, s);
+    if (e != cudaSuccess) return e;
+    e = gemm_tc(B, h, h, h1, h, wb + d.oW2(), h, EpiBiasGelu{w + d.ob2(), nullptr, h2, h}, err, s);
+    if (e != cudaSuccess) return e;
+    return gemm_tc(B, n_out, h, h2, h, wb + d.oW3(), h, EpiBiasOut{w + d.ob3(), y, n_out, y_shift, y_scale}, err, s);
 }
 
 cudaError_t mlp_forward(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,

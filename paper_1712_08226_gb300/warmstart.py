@@ -40,12 +40,14 @@ class WarmStartNet:
         self.y_shift = torch.zeros(self.n_out, **f32)
         self.y_scale = torch.ones(self.n_out, **f32)
         self.step = 0
+        self.use_tc = True          # prediction on the tensor cores (training stays on CUDA cores)
         self.sync()
 
     def c_struct(self):
         p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
         return _lib.HopfMlp(self.n_in, self.hidden, self.n_out, p(self.w), p(self.w_bf16), p(self.m), p(self.v),
-                            p(self.x_shift), p(self.x_scale), p(self.y_shift), p(self.y_scale))
+                            p(self.x_shift), p(self.x_scale), p(self.y_shift), p(self.y_scale),
+                            int(self.use_tc))
 
     def _stream(self):
         return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)

@@ -54,10 +54,39 @@ def test_forward_matches_oracle(H):
     import torch
     from oracle import mlp as om
     net, layers, (xs, xsc, ys, ysc) = _net_and_oracle()
+    net.use_tc = False
     x = np.random.default_rng(7).normal(0, 1.5, (77, 5))        # ragged vs the 64-row tile
     y = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
     ref = om.predict(layers, x, xs, xsc, ys, ysc)
     assert np.allclose(y, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(a, dtype=torch.float64).to(torch.bfloat16).double().numpy()
+
+
+@pytest.mark.parametrize("B,hidden", [(77, 24), (300, 256)])
+def test_tensor_core_forward_matches_bf16_model(H, B, hidden):
+    # The tcgen05 path multiplies bfloat16 activations by bfloat16 weights with
+    # float32 accumulation: the oracle rounds every layer input to bfloat16 the
+    # same way and must agree up to the summation order.
+    import torch
+    from oracle import mlp as om
+    net, layers, (xs, xsc, ys, ysc) = _net_and_oracle(hidden=hidden)
+    net.use_tc = True
+    x = np.random.default_rng(17).normal(0, 1.5, (B, 5))        # B not a multiple of 128
+    y = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    h = _bf16((x - xs) / xsc)
+    for li, (W, b) in enumerate(layers):
+        a = h @ W.T + b
+        h = _bf16(om.gelu(a)) if li + 1 < len(layers) else a
+    ref = h * ysc + ys
+    assert np.allclose(y, ref, rtol=2e-3, atol=2e-3 * np.abs(ref).max()), np.abs(y - ref).max()
+    # and it stays close to the float32 path
+    net.use_tc = False
+    y32 = net.forward(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.abs(y - y32).max() <= 0.05 * np.abs(y32).max()
 
 
 def test_gradient_matches_oracle(H):
