@@ -115,6 +115,11 @@ typedef struct {
                            in the second), or as soon as its phase has no new
                            point left to start.  0 = library default (4096);
                            < 0 = first phase only.                                */
+    int newton;         /* hopf_time_to_reach: 0 = bisection with certified signs;
+                           1 = the hybrid of §IV: Newton steps
+                           t + phi / H_x(p*, x) (Eq. 26) inside the certified
+                           bracket, midpoint when a step leaves it; every
+                           candidate is solved to tol_gap.                        */
 } hopf_opts;
 
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,

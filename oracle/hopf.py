@@ -377,6 +377,66 @@ def time_to_reach(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-8,
     return dict(T=T_out, p=p_out, status=st, steps=steps)
 
 
+def time_to_reach_newton(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-10, max_steps=100,
+                         max_iter=400000, sigma_scale=1.0):
+    """Minimum time to reach by the hybrid of §IV: Newton steps on phi(x, T)
+    using the HJ equation for the derivative, t_{k+1} = t_k + phi / H_x(p*, x0)
+    (Eq. 26 with H_x of §IV), safeguarded by the bracket [lo, hi] that the
+    certified signs of phi maintain; a step that leaves the bracket is replaced
+    by its midpoint.  Every candidate is solved to tol_gap.  Stops when a step
+    is below tol_T * t, the bracket is below tol_T * hi, or the certified
+    interval [-P, -D] contains 0 (|phi| below the gap).  Starts at t_max.
+    Returns dict(T, p, status, steps)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    P_, n = x.shape
+    Wi = np.linalg.inv(sysd["W"])
+    T_out = np.zeros(P_)
+    p_out = np.zeros((P_, n))
+    st = np.zeros(P_, dtype=np.int64)
+
+    def solve(idx, Tvals):
+        probs = [setup(sysd, float(Tv), N, rule, tau, sigma_scale) for Tv in Tvals]
+        return pdhg(_batched(probs), x[idx], tol=tol_gap, max_iter=max_iter)
+
+    inside = terminal_cost(sysd, x) <= 0.0
+    p_out[inside] = 2.0 * x[inside] @ Wi.T
+    todo = np.where(~inside)[0]
+    lo = np.zeros(P_)
+    hi = np.full(P_, float(t_max))
+    t = np.full(P_, float(t_max))
+    steps = 0
+    first = True
+    while todo.size and steps < max_steps:
+        steps += 1
+        r = solve(todo, t[todo])
+        Pv, Dv = r["P"], r["D"]
+        above = Pv < 0.0                  # phi >= -P > 0: not reached by t
+        below = Dv > 0.0                  # phi <= -D < 0: reached
+        if first:
+            unreach = todo[above]
+            st[unreach] = UNREACHABLE
+            T_out[unreach] = np.inf
+            first = False
+        p_out[todo] = r["p"]
+        T_out[todo] = t[todo]
+        lo[todo[above]] = t[todo[above]]
+        hi[todo[below]] = t[todo[below]]
+        # Newton step with the HJ derivative d phi / dT = -H_x(p*, x0)
+        H = hamiltonian_x(sysd, r["p"], x[todo])
+        phi = -Pv
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tn = t[todo] + phi / H
+        bad = ~np.isfinite(tn) | (tn <= lo[todo]) | (tn >= hi[todo])
+        tn = np.where(bad, 0.5 * (lo[todo] + hi[todo]), tn)
+        done = (~(above | below)) | (np.abs(tn - t[todo]) <= tol_T * tn) | \
+            (hi[todo] - lo[todo] <= tol_T * hi[todo])
+        if steps == 1:
+            done |= above                 # unreachable
+        t[todo] = np.where(done, t[todo], tn)
+        todo = todo[~done]
+    return dict(T=T_out, p=p_out, status=st, steps=steps)
+
+
 # ------------------------------------------------------------------ trajectory
 def optimal_control(sysd, p, s):
     """u*(s) = Q argmax_{c in U} <c, -Q^T B^T e^{-s A^T} p>  (Eq. 27), the control

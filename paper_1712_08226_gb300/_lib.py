@@ -19,7 +19,7 @@ class HopfOpts(ctypes.Structure):
     _fields_ = [("rule", c_int), ("N", c_int), ("max_iter", c_int), ("gap_every", c_int),
                 ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
                 ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int),
-                ("accel", c_int), ("park_iters", c_int)]
+                ("accel", c_int), ("park_iters", c_int), ("newton", c_int)]
 
 
 class HopfMlp(ctypes.Structure):

@@ -65,11 +65,13 @@ class Options:
     profile: bool = False
     accel: bool = False
     park_iters: int = 0
+    newton: bool = False
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
-                             int(self.profile), int(self.accel), int(self.park_iters))
+                             int(self.profile), int(self.accel), int(self.park_iters),
+                             int(self.newton))
 
 
 def _is_torch(a):

@@ -36,6 +36,13 @@ template <typename R>
 cudaError_t launch_ttr_init(int P, cudaStream_t s, const double *inst0, int n, int m, int N, const R *x,
                             const R *T_lo, const R *T_hi, double t_max, double *lo, double *hi, int *phase,
                             int *warm, int *st, double *Tfinal);
+cudaError_t launch_ttr_newton_start(int P, cudaStream_t s, const double *hi, const int *phase, double *cand,
+                                    int *active);
+template <typename R>
+cudaError_t launch_ttr_newton_update(int P, cudaStream_t s, int n, int m, int ctrl_kind, const double *A,
+                                     const double *B, const double *qd, const R *x, double t_max, double tol_T,
+                                     const R *Pv, const R *Dv, const R *pstar, double *cand, int *active, double *lo,
+                                     double *hi, int *phase, int *st, double *Tfinal, int *remaining);
 cudaError_t launch_ttr_candidates(int P, cudaStream_t s, const double *lo, const double *hi, const int *phase,
                                   double *cand, int *active);
 template <typename R>
@@ -267,6 +274,7 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
             return fail(HOPF_EINVAL, "need tau > 0 and 0 < sigma_scale <= 1");
         if (!(o->tol_gap >= 0.0)) return fail(HOPF_EINVAL, "bad tol_gap");
         if (o->accel != 0 && o->accel != 1) return fail(HOPF_EINVAL, "accel must be 0 or 1");
+        if (o->newton != 0 && o->newton != 1) return fail(HOPF_EINVAL, "newton must be 0 or 1");
     }
     return HOPF_SUCCESS;
 }
@@ -652,7 +660,28 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     const R *inst = fp32 ? (const R *)b.i32 : (const R *)b.i64;
     int steps = 0;
     const int max_steps = 256;
-    for (;;) {
+    if (o->newton) {
+        // hybrid Newton/bisection (§IV): every candidate solved to tol_gap
+        CU(launch_ttr_newton_start(P, s, b.hi, b.phase, b.cand, b.act));
+        prm.sign_mode = 0;
+        for (;;) {
+            rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
+            if (rc) return rc;
+            rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
+                                   b.act, s);
+            if (rc) return rc;
+            CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
+            CU(launch_ttr_newton_update<R>(P, s, n, m, pr->ctrl_kind, b.d.A, b.d.B, b.d.q, b.dx, o->t_max, o->tol_T,
+                                           b.Pv, b.Dv, b.ptmp, b.cand, b.act, b.lo, b.hi, b.phase, b.st, b.Tf,
+                                           b.rem));
+            int remaining = 0;
+            CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            ++steps;
+            if (remaining == 0 || steps >= max_steps) break;
+        }
+    }
+    for (; !o->newton;) {
         CU(launch_ttr_candidates(P, s, b.lo, b.hi, b.phase, b.cand, b.act));
         rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
         if (rc) return rc;

@@ -102,6 +102,74 @@ __global__ void ttr_update_kernel(int P, double t_max, double tol_T, const doubl
     atomicAdd(remaining, 1);
 }
 
+// Hybrid Newton/bisection of §IV (Eq. 26): every candidate is solved to the
+// gap tolerance; the certified signs keep the bracket [lo, hi]; the next
+// candidate is t + phi / H_x(p*, x0) with H_x(p, x0) = -x0^T A^T p + |-Q^T B^T p|_*
+// (d phi / dT = -H_x), or the bracket midpoint when that step leaves the
+// bracket.  A point stops when the step is below tol_T t, the bracket below
+// tol_T hi, or the certified interval [-P, -D] contains zero.
+__global__ void ttr_newton_start_kernel(int P, const double *hi, const int *phase, double *cand, int *active) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    active[k] = phase[k] != PH_DONE;
+    cand[k] = hi[k];
+}
+
+template <typename R>
+__global__ void ttr_newton_update_kernel(int P, int n, int m, int ctrl_kind, const double *__restrict__ A,
+                                         const double *__restrict__ B, const double *__restrict__ qd,
+                                         const R *__restrict__ x, double t_max, double tol_T, const R *Pv,
+                                         const R *Dv, const R *pstar, double *cand, int *active, double *lo,
+                                         double *hi, int *phase, int *st, double *Tfinal, int *remaining) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P || !active[k]) return;
+    const double Pk = (double)Pv[k], Dk = (double)Dv[k], t = cand[k];
+    const bool above = Pk < 0.0, below = Dk > 0.0;
+    if (phase[k] == PH_HI && above && t < t_max) {   // a warm bracket too short: restart from t_max
+        lo[k] = t;
+        hi[k] = t_max;
+        cand[k] = t_max;
+        atomicAdd(remaining, 1);
+        return;
+    }
+    if (phase[k] == PH_HI && above) {            // phi(t_max) > 0
+        st[k] = HOPF_UNREACHABLE;
+        Tfinal[k] = t_max;
+        phase[k] = PH_DONE;
+        active[k] = 0;
+        return;
+    }
+    if (above) lo[k] = t;
+    if (below) hi[k] = t;
+    const R *pk = pstar + (long long)k * n;
+    const R *xk = x + (long long)k * n;
+    double H = 0.0;                              // -x0^T A^T p = -(A x0) . p
+    for (int i = 0; i < n; ++i) {
+        double ax = 0.0;
+        for (int j = 0; j < n; ++j) ax = fma(A[i * n + j], (double)xk[j], ax);
+        H -= ax * (double)pk[i];
+    }
+    double nrm = 0.0;                            // |-Q^T B^T p|_*
+    for (int c = 0; c < m; ++c) {
+        double g = 0.0;
+        for (int i = 0; i < n; ++i) g = fma(B[i * m + c] * qd[c], (double)pk[i], g);
+        nrm += ctrl_kind == HOPF_BALL ? g * g : fabs(g);
+    }
+    H += ctrl_kind == HOPF_BALL ? sqrt(nrm) : nrm;
+    double tn = t + (-Pk) / H;
+    if (!isfinite(tn) || tn <= lo[k] || tn >= hi[k]) tn = 0.5 * (lo[k] + hi[k]);
+    const bool done = !(above || below) || fabs(tn - t) <= tol_T * tn || hi[k] - lo[k] <= tol_T * hi[k];
+    if (done) {
+        phase[k] = PH_DONE;
+        Tfinal[k] = t;
+        active[k] = 0;
+        return;
+    }
+    phase[k] = PH_BIS;
+    cand[k] = tn;
+    atomicAdd(remaining, 1);
+}
+
 template <typename R>
 __global__ void ttr_finish_kernel(int P, const int *st, const int *fst, const double *Tfinal,
                                   R *T_star, int *status) {
@@ -214,6 +282,23 @@ cudaError_t launch_ttr_update(int P, cudaStream_t s, double t_max, double tol_T,
     return cudaGetLastError();
 }
 
+cudaError_t launch_ttr_newton_start(int P, cudaStream_t s, const double *hi, const int *phase, double *cand,
+                                    int *active) {
+    ttr_newton_start_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, hi, phase, cand, active);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_ttr_newton_update(int P, cudaStream_t s, int n, int m, int ctrl_kind, const double *A,
+                                     const double *B, const double *qd, const R *x, double t_max, double tol_T,
+                                     const R *Pv, const R *Dv, const R *pstar, double *cand, int *active, double *lo,
+                                     double *hi, int *phase, int *st, double *Tfinal, int *remaining) {
+    ttr_newton_update_kernel<R><<<(P + 127) / 128, 128, 0, s>>>(P, n, m, ctrl_kind, A, B, qd, x, t_max, tol_T, Pv,
+                                                                Dv, pstar, cand, active, lo, hi, phase, st, Tfinal,
+                                                                remaining);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_ttr_finish(int P, cudaStream_t s, const int *st, const int *fst, const double *Tfinal,
                               R *T_star, int *status) {
@@ -236,6 +321,10 @@ cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const doubl
     template cudaError_t launch_ttr_update<R>(int, cudaStream_t, double, double, const double *,          \
                                               const int *, const R *, const R *, const int *, double *,   \
                                               double *, int *, int *, int *, double *, int *);            \
+    template cudaError_t launch_ttr_newton_update<R>(int, cudaStream_t, int, int, int, const double *,     \
+                                                     const double *, const double *, const R *, double, double, \
+                                                     const R *, const R *, const R *, double *, int *, double *, \
+                                                     double *, int *, int *, double *, int *);                  \
     template cudaError_t launch_ttr_finish<R>(int, cudaStream_t, const int *, const int *,                \
                                               const double *, R *, int *);                                \
     template cudaError_t launch_trajectory<R>(int, int, cudaStream_t, const double *, const double *,     \

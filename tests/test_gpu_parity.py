@@ -294,3 +294,53 @@ def test_random10_parking_through_all_phases(H, accel):
     err = rel_err(np_(r["phi"]), np.array(g["phi"]))
     assert err.max() <= 1e-5, err.max()
     assert (r["iters"].cpu().numpy() > 16 * 6).sum() > 10          # some finished in the last phase
+
+
+def test_di_time_to_reach_newton_fp64(H):
+    # §IV hybrid Newton/bisection against the oracle's bisection goldens, in
+    # fewer steps than the device bisection
+    import torch
+    g = gold("di_time_to_reach.json")
+    m = g["meta"]
+    w = wl.workload_di(m["P"])
+    sysd = H.System.from_dict(w["system"])
+    base = dict(N=m["N"], rule=H.TRAPEZOID, tau=m["tau"], tol_gap=1e-10, precision=H.FP64, t_max=m["t_max"],
+                tol_T=1e-7, max_iter=1000000)
+    xn = cuda(w["x"], torch.float64)
+    rn = H.time_to_reach(sysd, xn, H.Options(newton=True, **base))
+    rb = H.time_to_reach(sysd, xn, H.Options(newton=False, **dict(base, tol_gap=1e-8)))
+    T = np_(rn["T"])
+    Tg = np.array(g["T"])
+    assert np.all(rn["status"].cpu().numpy() == 0)
+    assert np.all(np.abs(T - Tg) <= 1e-4 * np.maximum(Tg, 1e-3)), np.max(np.abs(T - Tg) / Tg)
+    assert rn["steps"] < rb["steps"], (rn["steps"], rb["steps"])
+
+
+def test_newton_short_warm_bracket_restarts(H):
+    # a warm bracket whose top is below T* is detected and widened to t_max
+    n, r = 2, 0.5
+    sysd = H.System.from_dict(wl.single_integrator(n, 0, radius=1.0, radius_target=r))
+    x = np.array([[1.5, 0.2], [-2.0, 2.5], [3.0, -1.0]])
+    exact = np.linalg.norm(x, axis=1) - r
+    opts = H.Options(N=8, tau=1.0, t_max=6.0, tol_T=1e-7, tol_gap=1e-9, precision=H.FP64, newton=True)
+    import torch
+    lo = cuda(np.full(3, 0.1), torch.float64)
+    hi = cuda(np.full(3, 0.5), torch.float64)          # below every T*
+    res = H.time_to_reach(sysd, cuda(x, torch.float64), opts, T_lo=lo, T_hi=hi)
+    assert np.all(res["status"].cpu().numpy() == 0)
+    assert np.allclose(np_(res["T"]), exact, rtol=1e-4)
+
+
+def test_single_integrator_time_to_reach_newton_fp32(H):
+    # closed form T* = max(|x| - r, 0) for A = 0, B = I, unit ball; a point
+    # inside the target (T* = 0) and unreachable horizons included
+    n, r = 2, 0.5
+    sysd = H.System.from_dict(wl.single_integrator(n, 0, radius=1.0, radius_target=r))
+    x = np.array([[1.5, 0.2], [0.1, 0.2], [-2.0, 2.5], [3.0, -1.0]])
+    opts = H.Options(N=8, tau=1.0, t_max=6.0, tol_T=1e-6, tol_gap=1e-6, newton=True)
+    res = H.time_to_reach(sysd, cuda(x), opts)
+    exact = np.maximum(np.linalg.norm(x, axis=1) - r, 0.0)
+    assert np.allclose(np_(res["T"]), exact, rtol=1e-4, atol=1e-6)
+    opts.t_max = 1.0
+    st = H.time_to_reach(sysd, cuda(x), opts)["status"].cpu().numpy()
+    assert st[1] == 0 and st[2] == 3 and st[3] == 3

@@ -264,3 +264,18 @@ def test_accelerated_iteration_reaches_the_same_value():
     r1 = oh.value(sysd, x0, 1.0, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, accel=True)
     ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 32, "box", trapezoid=True)
     assert abs(r1["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
+
+
+def test_newton_time_to_reach_matches_closed_form_and_bisection():
+    # §IV hybrid Newton/bisection: single integrator closed form T* = |x| - r,
+    # and the double integrator against the bisection result.
+    sysd = wl.single_integrator(2, oh.BALL, radius=1.0, radius_target=0.5)
+    x = np.array([[1.5, 0.2], [0.1, 0.2], [-2.0, 2.5]])
+    r = oh.time_to_reach_newton(sysd, x, 6.0, 8, oh.LEFT_RIEMANN, tau=1.0, tol_T=1e-9)
+    assert np.allclose(r["T"], np.maximum(np.linalg.norm(x, axis=1) - 0.5, 0.0), rtol=1e-7, atol=1e-9)
+    sysd = wl.double_integrator(0.1)
+    x = np.array([[1.0, 0.5], [-1.2, 0.3], [0.4, -1.5]])
+    rn = oh.time_to_reach_newton(sysd, x, 10.0, 64, oh.TRAPEZOID, tau=2.0, tol_T=1e-8)
+    rb = oh.time_to_reach(sysd, x, 10.0, 64, oh.TRAPEZOID, tau=2.0, tol_T=1e-8)
+    assert np.allclose(rn["T"], rb["T"], rtol=1e-6), (rn["T"], rb["T"])
+    assert rn["steps"] < rb["steps"]
