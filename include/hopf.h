@@ -51,6 +51,8 @@ extern "C" {
 /* quadrature rules (§III.A, Eq. 17 and the trapezoid rule it mentions) */
 #define HOPF_LEFT_RIEMANN 0 /* t_i = i T/N, i = 0..N-1, weights T/N          */
 #define HOPF_TRAPEZOID 1    /* t_i = i T/(N-1), end weights halved           */
+#define HOPF_SIMPSON 2      /* composite Simpson: N odd, t_i = i T/(N-1),
+                               weights T/(3(N-1)) (1, 4, 2, 4, ..., 2, 4, 1)   */
 
 /* arithmetic of the iteration */
 #define HOPF_FP64 0 /* float64 everywhere                                    */
@@ -85,8 +87,8 @@ typedef struct {
 } hopf_problem;
 
 typedef struct {
-    int rule;           /* HOPF_LEFT_RIEMANN or HOPF_TRAPEZOID                    */
-    int N;              /* quadrature nodes (>= 1; >= 2 for the trapezoid rule)   */
+    int rule;           /* HOPF_LEFT_RIEMANN, HOPF_TRAPEZOID or HOPF_SIMPSON      */
+    int N;              /* quadrature nodes (>= 1; >= 2 trapezoid; odd >= 3 Simpson) */
     int max_iter;       /* iteration cap per solve                                */
     int gap_every;      /* duality-gap check period g (>= 1)                      */
     int precision;      /* HOPF_FP64 or HOPF_FP32                                 */

@@ -12,7 +12,7 @@ paper's own examples (§VI) are the double integrator and stacked copies of it.
 import numpy as np
 
 BALL, BOX = 0, 1
-LEFT_RIEMANN, TRAPEZOID = 0, 1
+LEFT_RIEMANN, TRAPEZOID, SIMPSON = 0, 1, 2
 
 
 def double_integrator(radius_target=0.1, u_max=1.0):

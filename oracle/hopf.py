@@ -37,7 +37,7 @@ import numpy as np
 from scipy.linalg import expm
 
 BALL, BOX = 0, 1
-LEFT_RIEMANN, TRAPEZOID = 0, 1
+LEFT_RIEMANN, TRAPEZOID, SIMPSON = 0, 1, 2
 
 OK, MAXITER, NONFINITE, UNREACHABLE, AMBIGUOUS_SIGN = 0, 1, 2, 3, 4
 
@@ -49,6 +49,8 @@ def nodes(T, N, rule):
     Left Riemann sum (§III.A, Eq. 17): t_i = i T/N, i = 0..N-1, weights T/N.
     Trapezoid rule (named in §III.A as an alternative): N samples including
     both ends, t_i = i T/(N-1), weights T/(N-1) with the two end weights halved.
+    Composite Simpson rule (also named there): N odd samples including both
+    ends, t_i = i h with h = T/(N-1), weights h/3 (1, 4, 2, 4, ..., 2, 4, 1).
     Returns (t, w)."""
     if rule == LEFT_RIEMANN:
         t = np.arange(N, dtype=np.float64) * (T / N)
@@ -59,6 +61,13 @@ def nodes(T, N, rule):
         w = np.full(N, h)
         w[0] *= 0.5
         w[-1] *= 0.5
+    elif rule == SIMPSON:
+        if N < 3 or N % 2 == 0:
+            raise ValueError("Simpson's rule needs an odd number of nodes >= 3")
+        h = T / (N - 1)
+        t = np.arange(N, dtype=np.float64) * h
+        w = np.where(np.arange(N) % 2 == 1, 4.0, 2.0) * (h / 3.0)
+        w[0] = w[-1] = h / 3.0
     else:
         raise ValueError("unknown quadrature rule")
     return t, w

@@ -266,8 +266,9 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
     if (!is_spd(pr->W, pr->n)) return fail(HOPF_ENOTSPD, "W is not symmetric positive definite");
     if (o->precision != HOPF_FP64 && o->precision != HOPF_FP32) return fail(HOPF_EINVAL, "bad precision");
     if (need_solver) {
-        if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID) return fail(HOPF_EINVAL, "bad rule");
-        if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2) || o->N > (1 << 20))
+        if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID && o->rule != HOPF_SIMPSON) return fail(HOPF_EINVAL, "bad rule");
+        if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2) ||
+            (o->rule == HOPF_SIMPSON && (o->N < 3 || o->N % 2 == 0)) || o->N > (1 << 20))
             return fail(HOPF_EINVAL, "bad node count N=%d", o->N);
         if (o->max_iter < 0 || o->gap_every < 1) return fail(HOPF_EINVAL, "bad max_iter or gap_every");
         if (!(o->tau > 0.0) || !(o->sigma_scale > 0.0) || !(o->sigma_scale <= 1.0))

@@ -118,8 +118,9 @@ int validate(const hopf_problem *pr, const hopf_opts *o) {
     if (!spd_small(pr->W, pr->n)) return HOPF_ENOTSPD;
     if (o->precision != HOPF_FP64 && o->precision != HOPF_FP32) return HOPF_EINVAL;
     if (o->host_io != 0) return HOPF_EINVAL;   // device arrays only: no staging buffers
-    if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID) return HOPF_EINVAL;
-    if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2)) return HOPF_EINVAL;
+    if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID && o->rule != HOPF_SIMPSON) return HOPF_EINVAL;
+    if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2) ||
+        (o->rule == HOPF_SIMPSON && (o->N < 3 || o->N % 2 == 0))) return HOPF_EINVAL;
     if (o->max_iter < 0 || o->gap_every < 1) return HOPF_EINVAL;
     if (!(o->tau > 0.0) || !(o->sigma_scale > 0.0) || !(o->sigma_scale <= 1.0)) return HOPF_EINVAL;
     if (!(o->tol_gap >= 0.0)) return HOPF_EINVAL;

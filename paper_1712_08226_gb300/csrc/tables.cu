@@ -40,7 +40,8 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         if (active && !active[inst]) continue;
         const double T = Tv[inst];
         double *o = out64 + (long long)inst * L.stride;
-        const double h = (rule == HOPF_TRAPEZOID) ? T / (double)(N - 1) : T / (double)N;
+        const bool ends = rule == HOPF_TRAPEZOID || rule == HOPF_SIMPSON;   // samples include t = T
+        const double h = ends ? T / (double)(N - 1) : T / (double)N;
 
         cta::expm(Eh, A, -h, n, X, T1, red);
         // G = B Q, Gram accumulator C = 0
@@ -49,7 +50,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         __syncthreads();
         double *cur = Ga, *nxt = Gb;
         for (int idx = 0; idx < N; ++idx) {
-            if (rule != HOPF_TRAPEZOID || idx > 0) {
+            if (!ends || idx > 0) {
                 cta::matmul(nxt, Eh, cur, n, n, m);     // advance s by h
                 double *t = cur; cur = nxt; nxt = t;
             }
@@ -70,6 +71,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             double wi = h;
             if (rule == HOPF_TRAPEZOID && (i == 0 || i == N - 1)) wi = 0.5 * h;
+            if (rule == HOPF_SIMPSON) wi = (i == 0 || i == N - 1) ? h / 3.0 : ((i & 1) ? 4.0 * h / 3.0 : 2.0 * h / 3.0);
             o[L.w + i] = wi;
         }
         // M = e^{-TA} W e^{-TA}^T (symmetrised), V = M^-1, S = (I + tau M / 2)^-1

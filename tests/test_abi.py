@@ -90,6 +90,8 @@ def test_rejects_non_finite_and_bad_options(lib):
     assert _call_value(lib, bad) == -5
     assert _call_value(lib, sysd, dict(tau=-1.0)) == -1
     assert _call_value(lib, sysd, dict(N=1, rule=1)) == -1
+    assert _call_value(lib, sysd, dict(N=8, rule=2)) == -1      # Simpson needs odd N
+    assert _call_value(lib, sysd, dict(N=9, rule=3)) == -1
     assert _call_value(lib, sysd, dict(sigma_scale=1.5)) == -1
     assert _call_value(lib, sysd, dict(gap_every=0)) == -1
     neg_box = dict(sysd)

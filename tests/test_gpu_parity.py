@@ -344,3 +344,21 @@ def test_single_integrator_time_to_reach_newton_fp32(H):
     opts.t_max = 1.0
     st = H.time_to_reach(sysd, cuda(x), opts)["status"].cpu().numpy()
     assert st[1] == 0 and st[2] == 3 and st[3] == 3
+
+
+def test_simpson_rule_fp32_small_kernel_and_fp64_generic(H):
+    # composite Simpson's rule (§III.A): node weights h/3 (1, 4, 2, ..., 4, 1)
+    import torch
+    from oracle import hopf as oh
+    w = wl.workload_random10(24)
+    sysd = H.System.from_dict(w["system"])
+    ref = oh.value(w["system"], w["x"], w["t"], 129, oh.SIMPSON, w["tau"], tol=1e-10)["phi"]
+    r = H.value(sysd, cuda(w["x"]), w["t"], H.Options(N=129, rule=H.SIMPSON, tau=w["tau"], tol_gap=1e-5))
+    assert np.all(r["status"].cpu().numpy() == 0)
+    assert rel_err(np_(r["phi"]), ref).max() <= 1e-5
+    d = wl.workload_di(16)
+    ref = oh.value(d["system"], d["x"], 1.5, 65, oh.SIMPSON, d["tau"], tol=1e-11)["phi"]
+    r = H.value(H.System.from_dict(d["system"]), cuda(d["x"], torch.float64), 1.5,
+                H.Options(N=65, rule=H.SIMPSON, tau=d["tau"], tol_gap=1e-11, precision=H.FP64, max_iter=1000000))
+    assert np.all(r["status"].cpu().numpy() == 0)
+    assert rel_err(np_(r["phi"]), ref).max() <= 1e-9

@@ -25,6 +25,29 @@ def test_nodes_left_riemann_and_trapezoid_integrate_polynomials():
     assert np.isclose(t[-1], 3.0) and np.isclose(w[0], 0.125)
 
 
+def test_simpson_weights_integrate_cubics_and_reject_even_counts():
+    # composite Simpson's rule (named in §III.A) is exact for cubics
+    t, w = oh.nodes(2.0, 9, oh.SIMPSON)
+    for k in range(4):
+        assert np.isclose((w * t ** k).sum(), 2.0 ** (k + 1) / (k + 1), rtol=1e-13)
+    assert not np.isclose((w * t ** 4).sum(), 2.0 ** 5 / 5, rtol=1e-6)
+    with pytest.raises(ValueError):
+        oh.nodes(2.0, 8, oh.SIMPSON)
+
+
+def test_simpson_value_converges_at_fourth_order():
+    # For a smooth Hamiltonian along the optimal p (ball control, K_i p != 0)
+    # the quadrature error of phi_N is that of the integral at p*: halving the
+    # step divides it by 16 with Simpson's rule and by 4 with the trapezoid
+    # rule.  A wrong Simpson weight pattern drops the order.
+    sysd = wl.random_system(5, 3, 2)
+    x = np.array([[4.2, -3.7, 3.9]])
+    ref = oh.value(sysd, x, 1.5, 1025, oh.SIMPSON, 0.5, tol=1e-13)["phi"][0]
+    for rule, order in ((oh.SIMPSON, 16.0), (oh.TRAPEZOID, 4.0)):
+        e = [abs(oh.value(sysd, x, 1.5, N, rule, 0.5, tol=1e-13)["phi"][0] - ref) for N in (9, 17, 33)]
+        assert all(abs(e[i] / e[i + 1] - order) < 0.1 * order for i in range(2)), (rule, e)
+
+
 # ----------------------------------------------------- double integrator table
 def test_di_node_matrices_closed_form():
     # §VI.A: A = [[0,1],[0,0]] is nilpotent, e^{-sA} B = [-s, 1]^T, so
