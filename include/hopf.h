@@ -122,7 +122,14 @@ typedef struct {
                            t + phi / H_x(p*, x) (Eq. 26) inside the certified
                            bracket, midpoint when a step leaves it; every
                            candidate is solved to tol_gap.                        */
+    int kernel;         /* hopf_value solve kernel: HOPF_KERNEL_AUTO (0) picks by
+                           size; HOPF_KERNEL_GENERIC (1) forces one warp per
+                           point (the reference layout of the iteration; used
+                           to compare the specialised kernels with it).          */
 } hopf_opts;
+
+#define HOPF_KERNEL_AUTO 0
+#define HOPF_KERNEL_GENERIC 1
 
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,
  * gap_every 8, FP32, device io, tau 1, sigma_scale 1 (§VI: sigma = 1/(tau |K|^2)),
@@ -151,6 +158,34 @@ int hopf_value(const hopf_problem *prob, const hopf_opts *opts, int P,
                const void *x, const void *t, int t_stride, const void *p_init,
                void *phi, void *p_star, void *gap, int *iters, int *status,
                void *stream);
+
+/*
+ * Stacked copies (§VI.B unscented control, §VI.C dimensional scaling): k
+ * copies of a base system (n_b states, m controls) driven by ONE shared
+ * control.  The stacked state is x = (chi_1, ..., chi_k) (n = k n_b),
+ * A~ = blockdiag(A, ..., A), B~ = (B; ...; B), and the target is
+ * {x : x^T W~^-1 x <= 1} with W~ = blockdiag(W_1, ..., W_k).
+ */
+typedef struct {
+    hopf_problem base;          /* n_b = base.n <= 8, m <= 16, A, B and the control
+                                   set of one copy; base.W is not used            */
+    int copies;                 /* k, 1 <= k <= 64                                */
+    const double *W_blocks;     /* host, k * n_b * n_b: the SPD blocks W_j        */
+} hopf_stacked;
+
+/*
+ * hopf_value_stacked - hopf_value for a stacked-copy system, with the
+ * structure used instead of the dense n x n stacked table: the node matrix of
+ * the stacked system is K~_i = (K_i, ..., K_i) (K_i of the base system,
+ * Eq. 20), so K~_i p = K_i (p_1 + ... + p_k) and K~^T y = (K^T y, ..., K^T y),
+ * |K~|^2 = k |K|^2, and M~, V~, S~ (Eq. 35, 37) are block diagonal.  Work per
+ * iteration and point: 4 N m n_b + O(k n_b^2).  Arguments, layouts and status
+ * as hopf_value with n = k n_b; per-point arrays must be device arrays
+ * (host_io = 0); accel must be 0.
+ */
+int hopf_value_stacked(const hopf_stacked *prob, const hopf_opts *opts, int P, const void *x,
+                       const void *t, int t_stride, const void *p_init, void *phi, void *p_star,
+                       void *gap, int *iters, int *status, void *stream);
 
 /*
  * hopf_time_to_reach - minimum time T* with phi(x, T*) <= 0 (§IV), by

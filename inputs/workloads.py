@@ -124,6 +124,65 @@ def workload_chain(P=4096):
                 rule=LEFT_RIEMANN, N=512, tol_gap=1e-5, samples=1000)
 
 
+def stacked_copies(base, k, block_scale):
+    """k copies of a base system driven by one shared control (§VI.B): state
+    (chi_1, ..., chi_k), A~ = blockdiag(A, ..., A), B~ = (B; ...; B); target
+    weight W = blockdiag(block_scale[j] I) (Omega = {x^T W^-1 x <= 1})."""
+    A, B = base["A"], base["B"]
+    nb = A.shape[0]
+    out = dict(base)
+    out["A"] = np.kron(np.eye(k), A)
+    out["B"] = np.kron(np.ones((k, 1)), B)
+    out["W"] = np.kron(np.diag(np.asarray(block_scale, dtype=np.float64)), np.eye(nb))
+    out["base"] = dict(base)
+    out["W_blocks"] = np.asarray(block_scale, dtype=np.float64)[:, None, None] * np.eye(nb)[None]
+    return out
+
+
+def unscented_samples(mu, std, kappa=1.0):
+    """2 d + 1 sigma points of N(mu, std^2 I) in d dimensions and their mean
+    weights (scaled unscented transform with alpha = 1, beta unused, kappa):
+    lambda = kappa, chi_0 = mu, chi_{+-j} = mu +- sqrt(d + lambda) std e_j,
+    w_0 = lambda / (d + lambda), w_j = 1 / (2 (d + lambda))."""
+    mu = np.asarray(mu, dtype=np.float64)
+    d = mu.shape[-1]
+    lam = kappa
+    h = np.sqrt(d + lam) * std
+    pts = [mu] + [mu + h * e for e in np.eye(d)] + [mu - h * e for e in np.eye(d)]
+    w = np.array([lam / (d + lam)] + [1.0 / (2.0 * (d + lam))] * (2 * d))
+    return np.stack(pts, axis=-2), w
+
+
+def workload_unscented(P=64, ell=0.1, std=0.0667, seed=12):
+    """§VI.B: the double integrator with an uncertain initial state N(mu, std^2 I)
+    represented by its 5 sigma points, one shared control (n = 10, m = 1 box).
+    Terminal cost sum_j w_j |chi_j|^2 - ell (the weighted mean square distance
+    to the origin) = ell (x^T W^-1 x - 1) with W = ell blockdiag(I / w_j): same
+    zero level set and time-to-reach as the paper's cost.  P query means
+    mu ~ U[-1, 1]^2; left Riemann, N = 100, tau = 0.5 (the paper's value).
+    The spread of the copies cannot be steered away, so phi(x, T) rises again
+    for large T; time-to-reach brackets on [0, 4], below that rise."""
+    mus = uniform_points(seed, P, 2, -1.0, 1.0)
+    chis, wm = unscented_samples(mus, std)
+    sysd = stacked_copies(double_integrator(0.1), len(wm), ell / wm)
+    return dict(name="unscented_double_integrator_n10", system=sysd, x=chis.reshape(P, -1), mu=mus,
+                weights=wm, ell=ell, rule=LEFT_RIEMANN, N=100, tau=0.5, tol_gap=1e-5, t_max=4.0)
+
+
+def workload_dimension(d, P=64, ell=0.1, std=0.0667, seed=13):
+    """§VI.C dimensional scaling: k = d / 2 double-integrator samples
+    chi_j ~ N(mu, std^2 I) (iid, seeded) sharing one control (n = d, m = 1 box),
+    terminal cost (1/k) sum_j |chi_j|^2 - ell, i.e. W = ell k I; P query means
+    mu ~ U[-1, 1]^2; left Riemann, N = 100, tau = 0.5."""
+    k = d // 2
+    rng = np.random.default_rng(seed)
+    mus = rng.uniform(-1.0, 1.0, (P, 2))
+    chis = mus[:, None, :] + std * rng.normal(0.0, 1.0, (P, k, 2))
+    sysd = stacked_copies(double_integrator(0.1), k, np.full(k, ell * k))
+    return dict(name=f"dimension_scaling_d{d}", system=sysd, x=chis.reshape(P, -1), mu=mus, ell=ell,
+                rule=LEFT_RIEMANN, N=100, tau=0.5, tol_gap=1e-5, t_max=10.0)
+
+
 def mlp_init(seed, sizes):
     """He-style initial weights for an MLP with the given layer sizes.  Returns a list
     of (W (out,in), b (out,)) pairs in float64."""

@@ -19,7 +19,8 @@ class HopfOpts(ctypes.Structure):
     _fields_ = [("rule", c_int), ("N", c_int), ("max_iter", c_int), ("gap_every", c_int),
                 ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
                 ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int),
-                ("accel", c_int), ("park_iters", c_int), ("newton", c_int)]
+                ("accel", c_int), ("park_iters", c_int), ("newton", c_int),
+                ("kernel", c_int)]
 
 
 class HopfMlp(ctypes.Structure):
@@ -28,7 +29,11 @@ class HopfMlp(ctypes.Structure):
                 ("y_shift", c_void_p), ("y_scale", c_void_p), ("use_tc", c_int)]
 
 
-EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_time_to_reach", "hopf_trajectory",
+class HopfStacked(ctypes.Structure):
+    _fields_ = [("base", HopfProblem), ("copies", c_int), ("W_blocks", P_double)]
+
+
+EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_value_stacked", "hopf_time_to_reach", "hopf_trajectory",
            "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile",
            "hopf_value_noalloc", "hopf_mlp_param_count", "hopf_mlp_sync", "hopf_mlp_forward",
            "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm", "hopf_tc_selftest")
@@ -51,6 +56,8 @@ def load(path=LIB_PATH):
     lib.hopf_value.argtypes = [PP, PO, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                c_void_p, c_void_p, c_void_p, c_void_p]
     lib.hopf_value.restype = c_int
+    lib.hopf_value_stacked.argtypes = [ctypes.POINTER(HopfStacked)] + lib.hopf_value.argtypes[1:]
+    lib.hopf_value_stacked.restype = c_int
     lib.hopf_time_to_reach.argtypes = [PP, PO, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p, P_int, c_void_p]
     lib.hopf_time_to_reach.restype = c_int

@@ -66,12 +66,13 @@ class Options:
     accel: bool = False
     park_iters: int = 0
     newton: bool = False
+    kernel: int = 0          # 0 auto, 1 force one warp per point
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
                              int(self.profile), int(self.accel), int(self.park_iters),
-                             int(self.newton))
+                             int(self.newton), int(self.kernel))
 
 
 def _is_torch(a):
@@ -138,6 +139,35 @@ def value(system, x, t, opts=None, p_init=None, stream=None):
     rc = lib.hopf_value(ctypes.byref(prob), ctypes.byref(o), P, mar.ptr(xx), mar.ptr(tt), 0 if scalar_t else 1,
                         mar.ptr(pi), mar.ptr(out["phi"]), mar.ptr(out["p"]), mar.ptr(out["gap"]),
                         mar.ptr(out["iters"]), mar.ptr(out["status"]), mar.stream(stream))
+    _check(lib, rc)
+    return out
+
+
+def value_stacked(base, W_blocks, x, t, opts=None, p_init=None, stream=None):
+    """phi for k copies of the base System sharing one control (§VI.B-C):
+    stacked state x = (chi_1, ..., chi_k) per row, target blockdiag(W_blocks)
+    (W_blocks: (k, n_b, n_b)); base.W is not used.  Device (torch) arrays
+    only.  Returns dict(phi, p, gap, iters, status)."""
+    lib = _lib.load()
+    opts = opts or Options()
+    if not _is_torch(x):
+        raise TypeError("value_stacked takes device (torch) arrays")
+    Wb = np.ascontiguousarray(W_blocks, dtype=np.float64)
+    k = int(Wb.shape[0])
+    mar = _Marshal(opts.precision, x)
+    xx = mar.inp(x)
+    P = int(xx.shape[0])
+    scalar_t = np.ndim(t) == 0 and not (_is_torch(t) and t.ndim > 0)
+    tt = mar.inp(np.array([float(t)]) if scalar_t else t)
+    pi = mar.inp(p_init)
+    out = dict(phi=mar.out((P,)), p=mar.out((P, k * base.n)), gap=mar.out((P,)),
+               iters=mar.out((P,), True), status=mar.out((P,), True))
+    sp = _lib.HopfStacked(base.c_struct(), k, Wb.ctypes.data_as(_lib.P_double))
+    o = opts.c_struct(False)
+    rc = lib.hopf_value_stacked(ctypes.byref(sp), ctypes.byref(o), P, mar.ptr(xx), mar.ptr(tt),
+                                0 if scalar_t else 1, mar.ptr(pi), mar.ptr(out["phi"]), mar.ptr(out["p"]),
+                                mar.ptr(out["gap"]), mar.ptr(out["iters"]), mar.ptr(out["status"]),
+                                mar.stream(stream))
     _check(lib, rc)
     return out
 

@@ -24,6 +24,18 @@ template <typename R>
 cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
                                 R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
                                 const int *active, cudaStream_t s);
+bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem);
+long long tile_workspace_floats(int n, int m, int N, int ppt, int grid);
+cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
+                             float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
+                             int ppt, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                           const double *qd, const double *W, int w_count, const double *Tv,
+                                           int n_inst, int n, int m, int N, int rule, double tau,
+                                           double sigma_scale, double *out64, float *out32, double *scratch);
+template <typename R>
+cudaError_t launch_pdhg_stacked(const R *inst, const SolveParams &prm, int k, const R *x, const R *p_init, R *phi,
+                                R *pstar, R *gap, int *iters, int *status, R *y, cudaStream_t s);
 cudaError_t launch_tc_selftest(int N, int K, const float *A, const float *B, float *D, int *err, cudaStream_t s);
 cudaError_t launch_pdhg_cta(int NS, int m, int grid, cudaStream_t s, const float *inst, const SolveParams &prm,
                             const float *x, float *phi, float *pstar, float *gap, int *iters, int *status,
@@ -276,6 +288,8 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
         if (!(o->tol_gap >= 0.0)) return fail(HOPF_EINVAL, "bad tol_gap");
         if (o->accel != 0 && o->accel != 1) return fail(HOPF_EINVAL, "accel must be 0 or 1");
         if (o->newton != 0 && o->newton != 1) return fail(HOPF_EINVAL, "newton must be 0 or 1");
+        if (o->kernel != HOPF_KERNEL_AUTO && o->kernel != HOPF_KERNEL_GENERIC)
+            return fail(HOPF_EINVAL, "kernel must be HOPF_KERNEL_AUTO or HOPF_KERNEL_GENERIC");
     }
     return HOPF_SUCCESS;
 }
@@ -479,18 +493,23 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     if (rc) return rc;
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     SmallPlan sp, sp32;
-    if (fp32 && t_stride == 0) {
+    if (fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO) {
         sp = plan_small(dev, n, m, N, P);
         sp32 = plan_small(dev, n, m, N, P, 32);
         sp32.grid = dev.sms;
     }
+    // large states, one shared table: the tiled kernel
+    int tile_ppt = 0, tile_grid = 0;
+    size_t tile_smem = 0;
+    const bool tile = fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !sp.ok && !o->accel &&
+                      tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem);
     const int tgrid = table_grid(dev, n_inst);
     const bool hio = o->host_io != 0;
     CarryPair cb;
 
     auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
                     R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
-                    int *&ctr) {
+                    int *&ctr, float *&tws) {
         d = take_problem(a, n, m);
         Tv = a.template take<double>(n_inst);
         i64 = a.template take<double>((size_t)n_inst * L.stride);
@@ -504,8 +523,9 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         dgap = hio ? a.template take<R>(P) : (R *)gap_;
         dit = hio ? a.template take<int>(P) : iters;
         dst = hio ? a.template take<int>(P) : status;
-        y = sp.ok ? nullptr : a.template take<R>((size_t)P * N * m);
+        y = (sp.ok || tile) ? nullptr : a.template take<R>((size_t)P * N * m);
         ctr = a.template take<int>(4);
+        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
     };
     DevProblem d;
@@ -513,13 +533,14 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     float *i32;
     R *dx, *dt, *dpi, *dphi, *dps, *dgap, *y;
     int *dit, *dst, *ctr;
+    float *tws;
     Arena meas(nullptr);
-    plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr);
+    plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
     void *base = nullptr;
     rc = ensure_workspace(meas.off, &base);
     if (rc) return rc;
     Arena a(base);
-    plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr);
+    plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
 
     rc = upload_problem(d, pr, s);
     if (rc) return rc;
@@ -553,6 +574,9 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         rc = run_small_two_phase(sp, sp32, m, (const float *)inst, prm, (const float *)dx, (const float *)dpi,
                                  (float *)dphi, (float *)dps, (float *)dgap, dit, dst, cb, o->park_iters, s);
         if (rc) return rc;
+    } else if (tile) {
+        CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)dx, (const float *)dpi, (float *)dphi,
+                            (float *)dps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem, s));
     } else {
         rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
         if (rc) return rc;
@@ -569,6 +593,68 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         CU(cudaMemcpyAsync(status, dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
     }
+    return HOPF_SUCCESS;
+}
+
+// ------------------------------------------------------- hopf_value_stacked
+__global__ void expand_horizons_kernel(const double *Tv, int nT, int k, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nT * k) out[i] = Tv[i / k];
+}
+
+template <typename R>
+int stacked_impl(const hopf_stacked *sp, const hopf_opts *o, int P, const void *x_, const void *t_, int t_stride,
+                 const void *pinit_, void *phi_, void *pstar_, void *gap_, int *iters, int *status,
+                 cudaStream_t s) {
+    const hopf_problem *pr = &sp->base;
+    const int nb = pr->n, m = pr->m, N = o->N, k = sp->copies;
+    const bool fp32 = o->precision == HOPF_FP32;
+    const int nT = t_stride ? P : 1;
+    const int n_inst = nT * k;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    const InstanceLayout L = InstanceLayout::make(nb, m, N);
+    const int tgrid = table_grid(dev, n_inst);
+    DevProblem d;
+    double *Wb, *Tv, *Tx, *i64, *tsc;
+    float *i32;
+    R *y;
+    auto plan = [&](Arena &a) {
+        d = take_problem(a, nb, m);
+        Wb = a.template take<double>((size_t)k * nb * nb);
+        Tv = a.template take<double>(nT);
+        Tx = a.template take<double>(n_inst);
+        i64 = a.template take<double>((size_t)n_inst * L.stride);
+        i32 = fp32 ? a.template take<float>((size_t)n_inst * L.stride) : nullptr;
+        tsc = a.template take<double>((size_t)tgrid * table_scratch_doubles(nb, m));
+        y = a.template take<R>((size_t)P * N * m);
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    std::vector<double> q(m);
+    for (int c = 0; c < m; ++c) q[c] = pr->ctrl_kind == HOPF_BALL ? pr->radius : pr->half_widths[c];
+    CU(cudaMemcpyAsync(d.A, pr->A, sizeof(double) * nb * nb, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d.B, pr->B, sizeof(double) * nb * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d.q, q.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(Wb, sp->W_blocks, sizeof(double) * k * nb * nb, cudaMemcpyHostToDevice, s));
+    CU(launch_horizons(nT, s, t_, fp32, Tv));
+    expand_horizons_kernel<<<(n_inst + 255) / 256, 256, 0, s>>>(Tv, nT, k, Tx);
+    CU(cudaGetLastError());
+    CU(launch_build_instances_wblocks(tgrid, table_threads(nb), s, d.A, d.B, d.q, Wb, k, Tx, n_inst, nb, m, N,
+                                      o->rule, o->tau, o->sigma_scale, i64, i32, tsc));
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.warm = pinit_ != nullptr;
+    prm.inst_stride = t_stride ? 1 : 0;
+    const R *inst = fp32 ? (const R *)i32 : (const R *)i64;
+    CU(launch_pdhg_stacked<R>(inst, prm, k, (const R *)x_, (const R *)pinit_, (R *)phi_, (R *)pstar_, (R *)gap_,
+                              iters, status, y, s));
     return HOPF_SUCCESS;
 }
 
@@ -662,13 +748,20 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     int steps = 0;
     const int max_steps = 256;
     if (o->newton) {
-        // hybrid Newton/bisection (§IV): every candidate solved to tol_gap
+        // hybrid Newton/bisection (§IV).  A candidate's solve stops as soon as
+        // the sign of phi is certified (or at tol_gap); the step uses the
+        // middle of the certified interval, so far from the root a loose
+        // solve gives an inexact Newton step and near it the solve tightens
+        // by itself.  After the first candidate every solve starts from the
+        // previous candidate's p*.
         CU(launch_ttr_newton_start(P, s, b.hi, b.phase, b.cand, b.act));
-        prm.sign_mode = 0;
+        prm.sign_mode = 1;
         for (;;) {
             rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
             if (rc) return rc;
-            rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
+            const R *p0 = steps == 0 ? b.dpi : b.ptmp;
+            prm.warm = p0 != nullptr;
+            rc = launch_generic<R>(inst, prm, b.dx, p0, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
                                    b.act, s);
             if (rc) return rc;
             CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
@@ -681,6 +774,7 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
             ++steps;
             if (remaining == 0 || steps >= max_steps) break;
         }
+        prm.warm = b.dpi != nullptr;
     }
     for (; !o->newton;) {
         CU(launch_ttr_candidates(P, s, b.lo, b.hi, b.phase, b.cand, b.act));
@@ -979,6 +1073,37 @@ int hopf_value(const hopf_problem *prob, const hopf_opts *opts, int P, const voi
     if (opts->precision == HOPF_FP64)
         return value_impl<double>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
     return value_impl<float>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+}
+
+int hopf_value_stacked(const hopf_stacked *prob, const hopf_opts *opts, int P, const void *x, const void *t,
+                       int t_stride, const void *p_init, void *phi, void *p_star, void *gap, int *iters, int *status,
+                       void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!prob || !opts) return fail(HOPF_EINVAL, "null problem or options");
+    const int nb = prob->base.n, k = prob->copies;
+    if (k < 1 || k > 64) return fail(HOPF_EINVAL, "copies must be in [1, 64]");
+    if (nb < 1 || nb > 8) return fail(HOPF_EINVAL, "the base state dimension must be in [1, 8]");
+    if (!prob->W_blocks) return fail(HOPF_EINVAL, "W_blocks is required");
+    hopf_problem first = prob->base;
+    first.W = prob->W_blocks;              // validate the base system with the first block
+    int rc = check_problem(&first, opts, true);
+    if (rc) return rc;
+    for (int j = 1; j < k; ++j) {
+        const double *Wj = prob->W_blocks + (long long)j * nb * nb;
+        if (!all_finite(Wj, (long long)nb * nb)) return fail(HOPF_ENONFINITE, "W block %d has a non-finite entry", j);
+        if (!is_spd(Wj, nb)) return fail(HOPF_ENOTSPD, "W block %d is not symmetric positive definite", j);
+    }
+    if (opts->host_io) return fail(HOPF_EINVAL, "hopf_value_stacked takes device arrays only (host_io = 0)");
+    if (opts->accel) return fail(HOPF_EINVAL, "hopf_value_stacked runs the iteration of Eq. 15 (accel = 0)");
+    if (P < 0) return fail(HOPF_EINVAL, "P must be >= 0");
+    if (P == 0) return HOPF_SUCCESS;
+    if (t_stride != 0 && t_stride != 1) return fail(HOPF_EINVAL, "t_stride must be 0 or 1");
+    if (!x || !t || !phi || !p_star || !gap || !iters || !status) return fail(HOPF_EINVAL, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (opts->precision == HOPF_FP64)
+        return stacked_impl<double>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+    return stacked_impl<float>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
 }
 
 int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P, const void *x, const void *T_lo,

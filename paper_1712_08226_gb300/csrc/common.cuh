@@ -91,3 +91,39 @@ __device__ __forceinline__ R rel_gap(R Pv, R Dv) {
 }
 
 }  // namespace hopf
+
+namespace hopf {
+
+// Geometry of the tiled large-state kernel (pdhg_tile.cu).  The control
+// dimension is padded to mp (exact: the extra rows of K are zero), each of the
+// 8 warps of a block owns npt consecutive nodes (rw = npt mp rows of K) of a
+// node block of nc = 8 npt nodes (cr rows), and the state dimension is padded
+// to n4 (a multiple of 4, zero columns) so rows can be read as float4.
+constexpr int TILE_WARPS = 8;
+struct TileGeom {
+    int mp, n4, nq, npt, rw, nc, cr, chunks, pt;
+};
+__host__ __device__ inline int tile_mpad(int m) {
+    return m <= 6 ? m : (m <= 8 ? 8 : (m <= 10 ? 10 : (m <= 12 ? 12 : 16)));
+}
+__host__ __device__ inline TileGeom tile_geom(int n, int m, int N, int ppt) {
+    TileGeom g;
+    g.mp = tile_mpad(m);
+    g.n4 = (n + 3) & ~3;
+    g.nq = g.n4 / 4;
+    g.npt = g.mp >= 8 ? 1 : 8 / g.mp;
+    g.rw = g.npt * g.mp;
+    g.nc = TILE_WARPS * g.npt;
+    g.cr = TILE_WARPS * g.rw;
+    g.chunks = (N + g.nc - 1) / g.nc;
+    g.pt = 32 * ppt;
+    return g;
+}
+// dynamic shared memory of one block, in floats: K block (also the u buffer
+// of the certificate), pbar tile, dual block, vector buffer, 3 per-slot sums
+__host__ __device__ inline long long tile_smem_floats(const TileGeom &g) {
+    const int kr = g.cr > g.pt ? g.cr : g.pt;
+    return (long long)kr * g.n4 + 2LL * g.n4 * g.pt + (long long)g.cr * g.pt + 3LL * g.pt;
+}
+
+}  // namespace hopf

@@ -1,0 +1,641 @@
+// Chambolle-Pock iteration (§III, Eq. 15 with theta = 1; prox of Eq. 22-23
+// and Eq. 37) for large state dimensions (16 < n <= 256, m <= 16), one node
+// table shared by every point, float32.
+//
+// The per-iteration work of a point is two products with the stacked table,
+// K pbar (G = N m rows) and K^T y, i.e. 4 G n flops on 2 G n table entries.
+// Warp-per-point reads the whole table from L2 for every point and iteration;
+// here a persistent block keeps a tile of 32 or 64 point slots and streams
+// node blocks of K through shared memory once per iteration for the whole
+// tile, so each table entry read feeds 2 x (tile) fused multiply-adds.
+//
+// Block layout: 8 warps.  In the K pbar product warp w owns npt consecutive
+// nodes of the node block (rw = npt mp rows of K) and lane l owns slots l and
+// l + 32; the m dot products of a (node, slot) pair end in one thread, which
+// then does the dual step and the projection onto w_i U in registers (ball:
+// radial scaling, box: clipping).  In the K^T y product warp w owns the state
+// quads q = w, w + 8, ... and accumulates them over all node blocks in
+// registers.  The dual variables of the slots live in a per-block global
+// buffer [row][slot] (coalesced across lanes); p and x0 of the slots in
+// per-block buffers [state][slot]; pbar in shared memory.
+//
+// Certificate (every gap_every iterations): P at the pbar the dual step used
+// (P = pbar^T M pbar / 4 + 1 - <x0, pbar> + sum_i w_i |K_i pbar|_*, the norm
+// sum taken from the dual step's products) and the Fenchel dual D at the new
+// feasible y, D = 1 - u^T V u with u = x0 - K^T y; both are bounds for any p
+// and any feasible y, so phi lies in [-P, -D].  A point stops when
+// (P - D)/max(1,|P|,|D|) plus the float rounding allowance is <= tol_gap.
+// For large n the float32 evaluation of P and D (quadratic forms over n^2
+// terms, K^T y over G rows, with cancellation when |phi| is large) can be off
+// by about 1e-5 relative, so a point that passes in float32 is re-certified:
+// P(pbar) and D(y) are evaluated once more in float64 from the float64 table
+// (y shrunk by 4e-7 so that float32 rounding cannot leave w_i U).  Only a
+// point whose float64 gap passes is accepted (phi = -P in float64); otherwise
+// it iterates on with its float32 acceptance threshold halved.  The slot of an
+// accepted point takes the next point from a global queue.
+#include "common.cuh"
+
+namespace hopf {
+
+namespace {
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
+__device__ __forceinline__ float comp(const float4 &v, int e) {
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// one-off: zero-padded float32 copies of K ([chunks cr][n4], row i mp + c for
+// node i and control component c), and of the symmetric S, M, V ([n][n4])
+__global__ void tile_pad_kernel(const float *__restrict__ inst, int n, int m, int N, TileGeom g,
+                                float *__restrict__ Kp, float *__restrict__ Sp, float *__restrict__ Mp,
+                                float *__restrict__ Vp) {
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    const long long nk = (long long)g.chunks * g.cr * g.n4;
+    const long long nm = (long long)n * g.n4;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk + 3 * nm; e += stride) {
+        if (e < nk) {
+            const long long row = e / g.n4;
+            const int j = (int)(e % g.n4);
+            const long long i = row / g.mp;
+            const int c = (int)(row % g.mp);
+            Kp[e] = (i < N && c < m && j < n) ? inst[L.K + (i * m + c) * n + j] : 0.f;
+        } else {
+            const long long f = e - nk;
+            const int which = (int)(f / nm);
+            const long long r = f % nm;
+            const int b = (int)(r / g.n4), a = (int)(r % g.n4);
+            const long long off = which == 0 ? L.S : (which == 1 ? L.M : L.V);
+            const float v = a < n ? inst[off + (long long)b * n + a] : 0.f;
+            (which == 0 ? Sp : (which == 1 ? Mp : Vp))[r] = v;
+        }
+    }
+}
+
+}  // namespace
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < TILE_WARPS; ++w) t += red[w];
+    return t;
+}
+
+template <int MP, int PPT>
+__global__ void __launch_bounds__(TILE_WARPS * 32, 1)
+pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst64, const float *__restrict__ Kp,
+                 const float *__restrict__ Sp,
+                 const float *__restrict__ Mp, const float *__restrict__ Vp, SolveParams prm,
+                 const float *__restrict__ x, const float *__restrict__ p_init, float *__restrict__ phi,
+                 float *__restrict__ pstar, float *__restrict__ gap_out, int *__restrict__ iters,
+                 int *__restrict__ status, float *__restrict__ slot_p, float *__restrict__ slot_x,
+                 float *__restrict__ slot_y, int *__restrict__ queue) {
+    constexpr int NPT = MP >= 8 ? 1 : 8 / MP;
+    constexpr int RW = NPT * MP;
+    constexpr int PT = 32 * PPT;
+    constexpr int NQW = 8;                          // n <= 256: at most 8 quads per warp
+    const int n = prm.n, m = prm.m, N = prm.N, P = prm.P;
+    const TileGeom g = tile_geom(n, m, N, PPT);
+    const int n4 = g.n4, nq = g.nq, CR = g.cr, NC = g.nc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    const float *wv = inst + L.w;
+    const float *sc = inst + L.sc;
+    const bool ball = prm.ctrl_kind == HOPF_BALL;
+
+    if (sc[SC_ZERO] != 0.f) {
+        // T = 0: phi = J_x(x) = x^T V x - 1 (V = W^-1), p* = 2 V x
+        const float *V = inst + L.V;
+        for (int k = blockIdx.x * blockDim.x + tid; k < P; k += gridDim.x * blockDim.x) {
+            const float *xk = x + (long long)k * n;
+            float J = -1.f;
+            for (int a = 0; a < n; ++a) {
+                float s = 0.f;
+                for (int b = 0; b < n; ++b) s = fmaf(V[a * n + b], xk[b], s);
+                pstar[(long long)k * n + a] = 2.f * s;
+                J = fmaf(xk[a], s, J);
+            }
+            phi[k] = J;
+            gap_out[k] = 0.f;
+            iters[k] = 0;
+            status[k] = HOPF_OK;
+        }
+        return;
+    }
+    const float sigma = sc[SC_SIGMA];
+    const float tau = (float)prm.tau;
+
+    extern __shared__ float4 smem4[];
+    float *Ks = reinterpret_cast<float *>(smem4);                  // [max(cr, pt)][n4]
+    float *Pb = Ks + (long long)(CR > PT ? CR : PT) * n4;         // [nq][pt][4]
+    float *VB = Pb + (long long)n4 * PT;                           // [n4][pt]
+    float *Ys = VB + (long long)n4 * PT;                           // [cr][pt]
+    float *Hs = Ys + (long long)CR * PT;                           // [pt]
+    float *Qs = Hs + PT, *Ds = Qs + PT;
+    __shared__ int sl_pt[PT], sl_cnt[PT], sl_fresh[PT], sl_done[PT];
+    __shared__ float sl_tol[PT];
+    __shared__ int s_check, s_active, s_verify;
+    __shared__ double red[TILE_WARPS];
+
+    float *ps = slot_p + (long long)blockIdx.x * n4 * PT;          // [n4][pt]
+    float *xs = slot_x + (long long)blockIdx.x * n4 * PT;
+    float *Yg = slot_y + (long long)blockIdx.x * g.chunks * CR * PT;  // [chunks cr][pt]
+    auto pb_at = [&](int j, int s) -> float & { return Pb[((j >> 2) * PT + s) * 4 + (j & 3)]; };
+
+    // fill every slot from the queue
+    if (tid < PT) {
+        const int k = atomicAdd(queue, 1);
+        sl_pt[tid] = k < P ? k : -1;
+        sl_cnt[tid] = 0;
+        sl_fresh[tid] = 1;
+        sl_done[tid] = 0;
+        sl_tol[tid] = (float)prm.tol_gap;
+    }
+    __syncthreads();
+    for (int e = tid; e < n4 * PT; e += blockDim.x) {
+        const int j = e / PT, s = e % PT;
+        const int k = sl_pt[s];
+        float xv = 0.f, pv = 0.f;
+        if (k >= 0 && j < n) {
+            xv = x[(long long)k * n + j];
+            pv = prm.warm ? p_init[(long long)k * n + j] : xv;
+        }
+        xs[j * PT + s] = xv;
+        ps[j * PT + s] = pv;
+        pb_at(j, s) = pv;
+    }
+    __syncthreads();
+
+    for (int git = 1;; ++git) {
+        if (tid < PT) {
+            Hs[tid] = 0.f;
+            Qs[tid] = 0.f;
+            Ds[tid] = 0.f;
+            if (sl_pt[tid] >= 0) ++sl_cnt[tid];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int chk = (git % prm.gap_every) == 0, act = 0;
+            for (int s = 0; s < PT; ++s)
+                if (sl_pt[s] >= 0) {
+                    ++act;
+                    if (sl_cnt[s] > prm.max_iter) chk = 1;
+                }
+            s_check = chk;
+            s_active = act;
+        }
+        __syncthreads();
+        if (s_active == 0) break;
+        const bool check = s_check != 0;
+
+        float4 R[PPT][NQW];
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp)
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) R[pp][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float hpart[PPT];
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) hpart[pp] = 0.f;
+
+        for (int c = 0; c < g.chunks; ++c) {
+            {   // node block c of K into shared memory
+                const float4 *src = reinterpret_cast<const float4 *>(Kp + (long long)c * CR * n4);
+                float4 *dst = reinterpret_cast<float4 *>(Ks);
+                for (int e = tid; e < CR * nq; e += blockDim.x) dst[e] = __ldg(src + e);
+            }
+            __syncthreads();
+            // K pbar for this warp's rows and this lane's slots
+            float acc[PPT][RW];
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp)
+#pragma unroll
+                for (int r = 0; r < RW; ++r) acc[pp][r] = 0.f;
+            {
+                const float4 *Kw = reinterpret_cast<const float4 *>(Ks) + (long long)warp * RW * nq;
+                const float4 *P4 = reinterpret_cast<const float4 *>(Pb);
+                for (int q = 0; q < nq; ++q) {
+                    float4 pv[PPT];
+#pragma unroll
+                    for (int pp = 0; pp < PPT; ++pp) pv[pp] = P4[q * PT + lane + 32 * pp];
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        const float4 kv = Kw[r * nq + q];
+#pragma unroll
+                        for (int pp = 0; pp < PPT; ++pp) acc[pp][r] = dot4(kv, pv[pp], acc[pp][r]);
+                    }
+                }
+            }
+            // dual step and projection, one (node, slot) pair per thread
+#pragma unroll
+            for (int t = 0; t < NPT; ++t) {
+                const int i = c * NC + warp * NPT + t;
+                const bool node_ok = i < N;
+                const float wi = node_ok ? __ldg(wv + i) : 0.f;
+                const int row = warp * RW + t * MP;
+                const long long grow = (long long)c * CR + row;
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) {
+                    const int s = lane + 32 * pp;
+                    float yn[MP];
+                    if (node_ok && sl_pt[s] >= 0) {
+                        float nt = 0.f;
+#pragma unroll
+                        for (int cc = 0; cc < MP; ++cc) {
+                            const float z = acc[pp][t * MP + cc];
+                            nt += ball ? z * z : fabsf(z);
+                        }
+                        if (check) hpart[pp] = fmaf(wi, ball ? sqrtf(nt) : nt, hpart[pp]);
+                        float yo[MP];
+                        if (!sl_fresh[s]) {
+#pragma unroll
+                            for (int cc = 0; cc < MP; ++cc) yo[cc] = Yg[(grow + cc) * PT + s];
+                        } else if (!prm.warm) {     // y0 = K p0 (§VI), unprojected
+#pragma unroll
+                            for (int cc = 0; cc < MP; ++cc) yo[cc] = acc[pp][t * MP + cc];
+                        } else {                    // y0 = w_i argmax_{c in U} <c, K_i p0>
+                            const float scl = nt > 0.f ? wi * rsqrtf(nt) : 0.f;
+#pragma unroll
+                            for (int cc = 0; cc < MP; ++cc) {
+                                const float z = acc[pp][t * MP + cc];
+                                yo[cc] = ball ? z * scl : (cc < m ? (z >= 0.f ? wi : -wi) : 0.f);
+                            }
+                        }
+                        float nu = 0.f;
+#pragma unroll
+                        for (int cc = 0; cc < MP; ++cc) {
+                            yn[cc] = fmaf(sigma, acc[pp][t * MP + cc], yo[cc]);
+                            nu = fmaf(yn[cc], yn[cc], nu);
+                        }
+                        if (ball) {
+                            const float scl = (nu > wi * wi) ? wi * rsqrtf(nu) : 1.f;
+#pragma unroll
+                            for (int cc = 0; cc < MP; ++cc) yn[cc] *= scl;
+                        } else {
+#pragma unroll
+                            for (int cc = 0; cc < MP; ++cc) yn[cc] = cc < m ? fminf(fmaxf(yn[cc], -wi), wi) : 0.f;
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < MP; ++cc) Yg[(grow + cc) * PT + s] = yn[cc];
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < MP; ++cc) yn[cc] = 0.f;
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < MP; ++cc) Ys[(row + cc) * PT + s] = yn[cc];
+                }
+            }
+            __syncthreads();
+            // K^T y over this node block: warp w, quads w, w + 8, ...
+            {
+                const float4 *K4 = reinterpret_cast<const float4 *>(Ks);
+                for (int r = 0; r < CR; ++r) {
+                    float yv[PPT];
+#pragma unroll
+                    for (int pp = 0; pp < PPT; ++pp) yv[pp] = Ys[r * PT + lane + 32 * pp];
+#pragma unroll
+                    for (int k = 0; k < NQW; ++k) {
+                        const int q = warp + 8 * k;
+                        if (q < nq) {
+                            const float4 kv = K4[r * nq + q];
+#pragma unroll
+                            for (int pp = 0; pp < PPT; ++pp) {
+                                R[pp][k].x = fmaf(kv.x, yv[pp], R[pp][k].x);
+                                R[pp][k].y = fmaf(kv.y, yv[pp], R[pp][k].y);
+                                R[pp][k].z = fmaf(kv.z, yv[pp], R[pp][k].z);
+                                R[pp][k].w = fmaf(kv.w, yv[pp], R[pp][k].w);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (check) {
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) atomicAdd(&Hs[lane + 32 * pp], hpart[pp]);
+        }
+        // v = p - tau K^T y + tau x0 (argument of the prox of Eq. 37) and, on
+        // certificate iterations, u = x0 - K^T y (in the K block buffer)
+        float *UB = Ks;
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+            const int s = lane + 32 * pp;
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) {
+                const int q = warp + 8 * k;
+                if (q < nq) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = 4 * q + e;
+                        const float xv = xs[j * PT + s], pv = ps[j * PT + s], r = comp(R[pp][k], e);
+                        VB[j * PT + s] = fmaf(tau, xv - r, pv);
+                        if (check) UB[j * PT + s] = xv - r;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (check) {
+            // pbar^T (M pbar / 4 - x0) and u^T V u, this warp's share of the state
+            float qp[PPT], dp[PPT];
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) qp[pp] = dp[pp] = 0.f;
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) {
+                const int q = warp + 8 * k;
+                if (q >= nq) break;
+                float4 mq[PPT], vq[PPT];
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) mq[pp] = vq[pp] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int b = 0; b < n; ++b) {
+                    const float4 m4 = __ldg(reinterpret_cast<const float4 *>(Mp + (long long)b * n4) + q);
+                    const float4 v4 = __ldg(reinterpret_cast<const float4 *>(Vp + (long long)b * n4) + q);
+#pragma unroll
+                    for (int pp = 0; pp < PPT; ++pp) {
+                        const int s = lane + 32 * pp;
+                        const float pb = pb_at(b, s), uv = UB[b * PT + s];
+                        mq[pp].x = fmaf(m4.x, pb, mq[pp].x);
+                        mq[pp].y = fmaf(m4.y, pb, mq[pp].y);
+                        mq[pp].z = fmaf(m4.z, pb, mq[pp].z);
+                        mq[pp].w = fmaf(m4.w, pb, mq[pp].w);
+                        vq[pp].x = fmaf(v4.x, uv, vq[pp].x);
+                        vq[pp].y = fmaf(v4.y, uv, vq[pp].y);
+                        vq[pp].z = fmaf(v4.z, uv, vq[pp].z);
+                        vq[pp].w = fmaf(v4.w, uv, vq[pp].w);
+                    }
+                }
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) {
+                    const int s = lane + 32 * pp;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int a = 4 * q + e;
+                        qp[pp] = fmaf(pb_at(a, s), fmaf(0.25f, comp(mq[pp], e), -xs[a * PT + s]), qp[pp]);
+                        dp[pp] = fmaf(UB[a * PT + s], comp(vq[pp], e), dp[pp]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) {
+                atomicAdd(&Qs[lane + 32 * pp], qp[pp]);
+                atomicAdd(&Ds[lane + 32 * pp], dp[pp]);
+            }
+            __syncthreads();
+        }
+        // stop decisions, one thread per slot
+        if (tid < PT) {
+            const int s = tid, k = sl_pt[s];
+            sl_done[s] = 0;
+            if (k >= 0) {
+                const int cnt = sl_cnt[s];
+                if (check && (cnt >= 2 || cnt > prm.max_iter)) {
+                    const float quad = Qs[s] + 1.f, H = Hs[s];
+                    const float Pv = quad + H, Dv = 1.f - Ds[s];
+                    const float gp = rel_gap(Pv, Dv);
+                    const float scl = fmaxf(1.f, fmaxf(fabsf(Pv), fabsf(Dv)));
+                    int st = -1;
+                    if (!isfinite(Pv) || !isfinite(Dv)) st = HOPF_NONFINITE;
+                    else if (gp + gap_allowance(quad, H, Dv, scl) <= sl_tol[s]) st = HOPF_OK;
+                    else if (cnt > prm.max_iter) st = HOPF_MAXITER;
+                    if (st == HOPF_OK) {
+                        sl_done[s] = 2;             // float64 re-certification below
+                    } else if (st >= 0) {
+                        phi[k] = -Pv;
+                        gap_out[k] = gp;
+                        iters[k] = cnt - 1;
+                        status[k] = st;
+                        sl_done[s] = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int v = 0;
+            for (int s = 0; s < PT; ++s) v |= sl_done[s] == 2;
+            s_verify = v;
+        }
+        __syncthreads();
+        if (s_verify) {
+            const double *K64 = inst64 + L.K, *M64 = inst64 + L.M, *V64 = inst64 + L.V, *w64 = inst64 + L.w;
+            double *ub = reinterpret_cast<double *>(Ys);            // n doubles (dual block is free here)
+            for (int s = 0; s < PT; ++s) {
+                if (sl_done[s] != 2) continue;                        // uniform: shared memory
+                // H = sum_i w_i |K_i pbar|_*
+                double hp = 0.0;
+                for (int i = tid; i < N; i += blockDim.x) {
+                    double nt = 0.0;
+                    for (int c = 0; c < m; ++c) {
+                        const double *Kr = K64 + ((long long)i * m + c) * n;
+                        double z = 0.0;
+                        for (int j = 0; j < n; ++j) z = fma(Kr[j], (double)pb_at(j, s), z);
+                        nt += ball ? z * z : fabs(z);
+                    }
+                    hp = fma(w64[i], ball ? sqrt(nt) : nt, hp);
+                }
+                const double H64 = block_sum(hp, red);
+                // u = x0 - K^T y (y shrunk into w_i U), then D = 1 - u^T V u
+                for (int j = tid; j < n; j += blockDim.x) {
+                    double r = 0.0;
+                    for (int i = 0; i < N; ++i)
+                        for (int c = 0; c < m; ++c)
+                            r = fma(K64[((long long)i * m + c) * n + j],
+                                    (double)Yg[((long long)i * MP + c) * PT + s], r);
+                    ub[j] = (double)xs[j * PT + s] - (1.0 - 4e-7) * r;
+                }
+                __syncthreads();
+                double qp = 0.0, dp = 0.0;
+                for (int a = tid; a < n; a += blockDim.x) {
+                    double mq = 0.0, vq = 0.0;
+                    for (int b = 0; b < n; ++b) {
+                        mq = fma(M64[(long long)a * n + b], (double)pb_at(b, s), mq);
+                        vq = fma(V64[(long long)a * n + b], ub[b], vq);
+                    }
+                    qp = fma((double)pb_at(a, s), 0.25 * mq - (double)xs[a * PT + s], qp);
+                    dp = fma(ub[a], vq, dp);
+                }
+                const double quad64 = block_sum(qp, red) + 1.0;
+                const double D64 = 1.0 - block_sum(dp, red);
+                const double P64 = quad64 + H64;
+                const double g64 = rel_gap(P64, D64);
+                const double scl = fmax(1.0, fmax(fabs(P64), fabs(D64)));
+                if (tid == 0) {
+                    if (g64 + gap_allowance(quad64, H64, D64, scl) <= prm.tol_gap) {
+                        const int k = sl_pt[s];
+                        phi[k] = (float)(-P64);
+                        gap_out[k] = (float)g64;
+                        iters[k] = sl_cnt[s] - 1;
+                        status[k] = HOPF_OK;
+                        sl_done[s] = 1;
+                    } else {
+                        sl_done[s] = 0;
+                        sl_tol[s] *= 0.5f;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // p* of finished slots (the pbar of the certificate), then the prox
+        // S v of Eq. 37 for every slot
+        for (int e = tid; e < n * PT; e += blockDim.x) {
+            const int s = e / n, a = e % n;
+            if (sl_done[s]) pstar[(long long)sl_pt[s] * n + a] = pb_at(a, s);
+        }
+        float4 pn[PPT][NQW];
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp)
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) pn[pp][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NQW; ++k) {
+            const int q = warp + 8 * k;
+            if (q >= nq) break;
+            for (int b = 0; b < n; ++b) {
+                const float4 s4 = __ldg(reinterpret_cast<const float4 *>(Sp + (long long)b * n4) + q);
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) {
+                    const float v = VB[b * PT + lane + 32 * pp];
+                    pn[pp][k].x = fmaf(s4.x, v, pn[pp][k].x);
+                    pn[pp][k].y = fmaf(s4.y, v, pn[pp][k].y);
+                    pn[pp][k].z = fmaf(s4.z, v, pn[pp][k].z);
+                    pn[pp][k].w = fmaf(s4.w, v, pn[pp][k].w);
+                }
+            }
+        }
+        __syncthreads();
+        // p <- S v, pbar <- 2 p_new - p_old for the slots that go on
+#pragma unroll
+        for (int pp = 0; pp < PPT; ++pp) {
+            const int s = lane + 32 * pp;
+            if (sl_pt[s] < 0 || sl_done[s]) continue;
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) {
+                const int q = warp + 8 * k;
+                if (q < nq) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = 4 * q + e;
+                        const float pnew = comp(pn[pp][k], e);
+                        const float pold = ps[j * PT + s];
+                        ps[j * PT + s] = pnew;
+                        pb_at(j, s) = fmaf(2.f, pnew, -pold);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // finished slots take the next point
+        if (tid < PT) {
+            const int s = tid;
+            if (sl_done[s]) {
+                const int k = atomicAdd(queue, 1);
+                sl_pt[s] = k < P ? k : -1;
+                sl_cnt[s] = 0;
+                sl_fresh[s] = 1;
+                sl_tol[s] = (float)prm.tol_gap;
+            } else {
+                sl_fresh[s] = 0;
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < n4 * PT; e += blockDim.x) {
+            const int j = e / PT, s = e % PT;
+            if (!sl_done[s]) continue;
+            const int k = sl_pt[s];
+            float xv = 0.f, pv = 0.f;
+            if (k >= 0 && j < n) {
+                xv = x[(long long)k * n + j];
+                pv = prm.warm ? p_init[(long long)k * n + j] : xv;
+            }
+            xs[j * PT + s] = xv;
+            ps[j * PT + s] = pv;
+            pb_at(j, s) = pv;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ host side
+bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem) {
+    if (n < 1 || n > 256 || m < 1 || m > 16 || N < 1 || P < 1) return false;
+    for (int cand = 2; cand >= 1; --cand) {
+        const TileGeom g = tile_geom(n, m, N, cand);
+        const size_t bytes = (size_t)tile_smem_floats(g) * sizeof(float);
+        if (bytes > smem_limit) continue;
+        const int tiles = (P + g.pt - 1) / g.pt;
+        if (cand == 2 && tiles < sms) continue;     // prefer more blocks over wider tiles
+        *ppt = cand;
+        *grid = tiles < sms ? tiles : sms;
+        *smem = bytes;
+        return true;
+    }
+    return false;
+}
+
+// workspace floats: padded K, S, M, V; per-block p, x0 and dual buffers
+long long tile_workspace_floats(int n, int m, int N, int ppt, int grid) {
+    const TileGeom g = tile_geom(n, m, N, ppt);
+    return (long long)g.chunks * g.cr * g.n4 + 3LL * n * g.n4 + 2LL * grid * g.n4 * g.pt +
+           (long long)grid * g.chunks * g.cr * g.pt + 16;
+}
+
+template <int MP, int PPT>
+static cudaError_t launch_tile_t(const float *inst, const double *inst64, const float *Kp, const float *Sp, const float *Mp,
+                                 const float *Vp, const SolveParams &prm, const float *x, const float *p_init,
+                                 float *phi, float *pstar, float *gap, int *iters, int *status, float *sp,
+                                 float *sx, float *sy, int *queue, int grid, size_t smem, cudaStream_t s) {
+    auto kern = pdhg_tile_kernel<MP, PPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, TILE_WARPS * 32, smem, s>>>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters,
+                                             status, sp, sx, sy, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
+                             float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
+                             int ppt, int grid, size_t smem, cudaStream_t s) {
+    const int n = prm.n, m = prm.m, N = prm.N;
+    const TileGeom g = tile_geom(n, m, N, ppt);
+    float *Kp = ws;
+    float *Sp = Kp + (long long)g.chunks * g.cr * g.n4;
+    float *Mp = Sp + (long long)n * g.n4;
+    float *Vp = Mp + (long long)n * g.n4;
+    float *sp = Vp + (long long)n * g.n4;
+    float *sx = sp + (long long)grid * g.n4 * g.pt;
+    float *sy = sx + (long long)grid * g.n4 * g.pt;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    tile_pad_kernel<<<256, 256, 0, s>>>(inst, n, m, N, g, Kp, Sp, Mp, Vp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+#define TILE_CASE(MPV)                                                                                        \
+    case MPV:                                                                                                 \
+        return ppt == 2 ? launch_tile_t<MPV, 2>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
+                                                status, sp, sx, sy, queue, grid, smem, s)                    \
+                        : launch_tile_t<MPV, 1>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
+                                                status, sp, sx, sy, queue, grid, smem, s);
+    switch (g.mp) {
+        TILE_CASE(1)
+        TILE_CASE(2)
+        TILE_CASE(3)
+        TILE_CASE(4)
+        TILE_CASE(5)
+        TILE_CASE(6)
+        TILE_CASE(8)
+        TILE_CASE(10)
+        TILE_CASE(12)
+        TILE_CASE(16)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TILE_CASE
+}
+
+}  // namespace hopf

@@ -23,7 +23,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                                        const double *__restrict__ Tv, const int *__restrict__ active,
                                        int n_inst, int n, int m, int N, int rule, double tau,
                                        double sigma_scale, double *out64, float *out32,
-                                       double *scratch, bool smem_scratch) {
+                                       double *scratch, bool smem_scratch, int w_count) {
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     // scratch in shared memory when the launch provides it (small n), else global
     extern __shared__ double tsm[];
@@ -76,7 +76,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         }
         // M = e^{-TA} W e^{-TA}^T (symmetrised), V = M^-1, S = (I + tau M / 2)^-1
         cta::expm(ET, A, -T, n, X, T1, red);
-        cta::matmul(T2, ET, W, n, n, n);
+        cta::matmul(T2, ET, W + (long long)(inst % w_count) * n * n, n, n, n);
         cta::matmul_bt(T1, T2, ET, n, n, n);
         double *Mo = o + L.M, *Vo = o + L.V, *So = o + L.S;
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -154,7 +154,20 @@ cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const 
     const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
-                                                                      tau, sigma_scale, out64, out32, scratch, in_smem);
+                                                                      tau, sigma_scale, out64, out32, scratch, in_smem, 1);
+    return cudaGetLastError();
+}
+
+// instance k uses the target weight block W + (k % w_count) n^2 (stacked copies)
+cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                           const double *qd, const double *W, int w_count, const double *Tv,
+                                           int n_inst, int n, int m, int N, int rule, double tau,
+                                           double sigma_scale, double *out64, float *out32, double *scratch) {
+    const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
+    const bool in_smem = bytes <= 48 * 1024;
+    build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, nullptr, n_inst, n, m, N,
+                                                                      rule, tau, sigma_scale, out64, out32, scratch,
+                                                                      in_smem, w_count);
     return cudaGetLastError();
 }
 

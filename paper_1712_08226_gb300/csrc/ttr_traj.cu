@@ -102,11 +102,12 @@ __global__ void ttr_update_kernel(int P, double t_max, double tol_T, const doubl
     atomicAdd(remaining, 1);
 }
 
-// Hybrid Newton/bisection of §IV (Eq. 26): every candidate is solved to the
-// gap tolerance; the certified signs keep the bracket [lo, hi]; the next
-// candidate is t + phi / H_x(p*, x0) with H_x(p, x0) = -x0^T A^T p + |-Q^T B^T p|_*
-// (d phi / dT = -H_x), or the bracket midpoint when that step leaves the
-// bracket.  A point stops when the step is below tol_T t, the bracket below
+// Hybrid Newton/bisection of §IV (Eq. 26): every candidate is solved until
+// the sign of phi is certified (or to the gap tolerance); the certified signs
+// keep the bracket [lo, hi]; the next candidate is t + phi / H_x(p*, x0) with
+// phi the middle of the certified interval and H_x(p, x0) =
+// -x0^T A^T p + |-Q^T B^T p|_* (d phi / dT = -H_x), or the bracket midpoint
+// when that step leaves the bracket.  A point stops when the step is below tol_T t, the bracket below
 // tol_T hi, or the certified interval [-P, -D] contains zero.
 __global__ void ttr_newton_start_kernel(int P, const double *hi, const int *phase, double *cand, int *active) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,7 +157,7 @@ __global__ void ttr_newton_update_kernel(int P, int n, int m, int ctrl_kind, con
         nrm += ctrl_kind == HOPF_BALL ? g * g : fabs(g);
     }
     H += ctrl_kind == HOPF_BALL ? sqrt(nrm) : nrm;
-    double tn = t + (-Pk) / H;
+    double tn = t - 0.5 * (Pk + Dk) / H;         // phi estimate: middle of [-P, -D]
     if (!isfinite(tn) || tn <= lo[k] || tn >= hi[k]) tn = 0.5 * (lo[k] + hi[k]);
     const bool done = !(above || below) || fabs(tn - t) <= tol_T * tn || hi[k] - lo[k] <= tol_T * hi[k];
     if (done) {

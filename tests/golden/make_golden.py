@@ -70,8 +70,37 @@ def box_values(P=200):
          x=x, phi=r["phi"], p=r["p"])
 
 
+def chain10_time_to_reach(P=4):
+    # larger-state box-control system: chain of 10 masses (n = 20, m = 2)
+    sysd = wl.spring_chain(masses=10, actuators=2, radius_target=1.0)
+    x = wl.normal_points(11, P, 20, 0.7)
+    r = oh.time_to_reach(sysd, x, 20.0, 48, oh.LEFT_RIEMANN, tau=0.5, tol_T=1e-7, tol_gap=1e-8)
+    assert np.all(r["status"] == oh.OK)
+    dump("chain10_time_to_reach.json",
+         dict(source="oracle.hopf.time_to_reach", workload="10-mass spring chain (n=20, m=2 box), r=1, "
+              "x~N(0,0.49 I) seed 11", P=P, t_max=20.0, N=48, rule="left_riemann", tau=0.5, oracle_tol_T=1e-7),
+         x=x, T=r["T"], p=r["p"], status=r["status"])
+
+
+def unscented_time_to_reach(P=3):
+    # §VI.B: double integrator with 5 sigma points sharing one control (n = 10)
+    w = wl.workload_unscented(P)
+    r = oh.time_to_reach(w["system"], w["x"], w["t_max"], w["N"], w["rule"], tau=w["tau"], tol_T=1e-7,
+                         tol_gap=1e-8)
+    assert np.all(r["status"] == oh.OK)
+    dump("unscented_time_to_reach.json",
+         dict(source="oracle.hopf.time_to_reach", workload="unscented double integrator (n=10, m=1 box), "
+              "mu~U[-2,2]^2 seed 12, std 0.0667, ell 0.01", P=P, t_max=w["t_max"], N=w["N"], rule="left_riemann",
+              tau=w["tau"], oracle_tol_T=1e-7),
+         T=r["T"], p=r["p"], status=r["status"])
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["random10", "di", "ttr", "box"]
+    which = sys.argv[1:] or ["random10", "di", "ttr", "box", "chain10", "unscented"]
+    if "unscented" in which:
+        unscented_time_to_reach()
+    if "chain10" in which:
+        chain10_time_to_reach()
     if "box" in which:
         box_values()
     if "di" in which:

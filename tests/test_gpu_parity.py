@@ -362,3 +362,32 @@ def test_simpson_rule_fp32_small_kernel_and_fp64_generic(H):
                 H.Options(N=65, rule=H.SIMPSON, tau=d["tau"], tol_gap=1e-11, precision=H.FP64, max_iter=1000000))
     assert np.all(r["status"].cpu().numpy() == 0)
     assert rel_err(np_(r["phi"]), ref).max() <= 1e-9
+
+
+@pytest.mark.parametrize("newton", [False, True])
+def test_chain10_time_to_reach_fp32_against_oracle(H, newton):
+    # a larger box-control state (n = 20 > 16: per-point tables, one warp per
+    # point) through bisection and through the Newton hybrid
+    g = gold("chain10_time_to_reach.json")
+    m = g["meta"]
+    sysd = H.System.from_dict(wl.spring_chain(masses=10, actuators=2, radius_target=1.0))
+    opts = H.Options(N=m["N"], tau=m["tau"], t_max=m["t_max"], tol_T=1e-5, tol_gap=1e-5, newton=newton,
+                     max_iter=400000)
+    r = H.time_to_reach(sysd, cuda(g["x"]), opts)
+    # 4 = AMBIGUOUS_SIGN: a candidate's certified interval still straddled 0
+    # at the float32 floor gap (counted as reached, within tol of the root)
+    assert np.all(np.isin(r["status"].cpu().numpy(), (0, 4))), r["status"]
+    Tg = np.array(g["T"])
+    assert np.all(np.abs(np_(r["T"]) - Tg) <= 1e-4 * Tg), (np_(r["T"]), Tg)
+
+
+def test_unscented_time_to_reach_fp32_against_oracle(H):
+    # §VI.B: five sigma-point copies of the double integrator under one control
+    g = gold("unscented_time_to_reach.json")
+    m = g["meta"]
+    w = wl.workload_unscented(m["P"])
+    opts = H.Options(N=m["N"], tau=m["tau"], t_max=m["t_max"], tol_T=1e-5, tol_gap=1e-5, max_iter=400000)
+    r = H.time_to_reach(H.System.from_dict(w["system"]), cuda(w["x"]), opts)
+    assert np.all(np.isin(r["status"].cpu().numpy(), (0, 4))), r["status"]
+    Tg = np.array(g["T"])
+    assert np.all(np.abs(np_(r["T"]) - Tg) <= 1e-4 * Tg), (np_(r["T"]), Tg)

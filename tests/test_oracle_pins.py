@@ -302,3 +302,26 @@ def test_newton_time_to_reach_matches_closed_form_and_bisection():
     rb = oh.time_to_reach(sysd, x, 10.0, 64, oh.TRAPEZOID, tau=2.0, tol_T=1e-8)
     assert np.allclose(rn["T"], rb["T"], rtol=1e-6), (rn["T"], rb["T"])
     assert rn["steps"] < rb["steps"]
+
+
+# ------------------------------------------- stacked copies (§VI.B, §VI.C)
+def test_unscented_samples_reproduce_mean_and_covariance():
+    mu = np.array([0.7, -1.2])
+    chi, w = wl.unscented_samples(mu, 0.3)
+    assert chi.shape == (5, 2) and np.isclose(w.sum(), 1.0)
+    assert np.allclose(w @ chi, mu)
+    d = chi - mu
+    assert np.allclose((w[:, None] * d).T @ d, 0.09 * np.eye(2))
+
+
+def test_identical_stacked_copies_reduce_to_the_base_problem():
+    # All copies at the same state under one shared control: the weighted mean
+    # square distance is the base distance, so phi of the stacked problem
+    # equals phi of the base problem with target radius sqrt(ell), for any
+    # copy weights summing to 1.
+    w = wl.workload_unscented(3, std=0.0)
+    base = wl.double_integrator(np.sqrt(w["ell"]))
+    for T in (1.0, 2.5):
+        a = oh.value(w["system"], w["x"], T, 40, oh.LEFT_RIEMANN, 0.5, tol=1e-11)["phi"]
+        b = oh.value(base, w["mu"], T, 40, oh.LEFT_RIEMANN, 0.5, tol=1e-11)["phi"]
+        assert np.allclose(a, b, rtol=1e-8), (a, b)
