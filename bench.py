@@ -13,6 +13,9 @@ solves (the paper's iteration of Eq. 15, and the accelerated one) on the same
 GB300 for comparison.  Inputs are seeded and synthetic.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --workload chain|dimension ...   (secondary workloads: the
+       100-mass spring chain on the tiled large-state kernel; 60 stacked
+       double-integrator copies on the structured stacked-copy kernel)
 Under torchrun each rank solves its own 65,536 points (weak scaling, no
 collective on the data path; one barrier and a max-reduction of the timings).
 The reference arm times the FP64 CPU oracle on the host cores on a bounded
@@ -174,6 +177,181 @@ def train_warm_start(H, sysd, w, rank):
     return net, info
 
 
+def oracle_sample_seconds(code_body, timeout=900):
+    """Runs an oracle timing snippet in a fresh single-threaded process; it
+    prints one JSON dict with dt (s) and ok (certified points)."""
+    code = f"import os, sys, time, json\nsys.path.insert(0, {ROOT!r})\n" + code_body
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+SECONDARY = {
+    # 100-mass spring chain, value at a shared horizon: the tiled large-state kernel
+    "chain": dict(points=4096, T=10.0, N=512, tau=0.5, cpu_points=1),
+    # 60 double-integrator samples sharing one control (d = 120): the structured
+    # stacked-copy solve, with the dense stacked system as comparison
+    "dimension": dict(points=16384, T=2.5, d=120, cpu_points=2),
+}
+
+
+def run_secondary(args):
+    """One JSON line for a secondary workload (same timing rules as the
+    headline: W warm-up steps, K timed steps, L2 flushed before each, CUDA
+    events on the launching stream, clocks sampled)."""
+    cfg = SECONDARY[args.workload]
+    rank, world, local = rank_env()
+    points = args.points if args.points != POINTS else cfg["points"]
+    if args.workload == "chain":
+        sysd = wl.spring_chain()
+        x = wl.normal_points(3 + 1000 * rank, points, 200, 1.0)
+        n, m, N, T, tau = 200, 10, cfg["N"], cfg["T"], cfg["tau"]
+        fpi = flops_per_point_iter(n, m, N)
+        wname = f"spring_chain_n200_m10_box_N512_T10_{points}pts"
+        kernel = "pdhg_tile_kernel<10,1>"
+        cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
+                    f"x = wl.normal_points(3, {cfg['cpu_points']}, 200, 1.0)\nt0 = time.perf_counter()\n"
+                    f"r = oh.value(wl.spring_chain(), x, {T}, {N}, oh.LEFT_RIEMANN, tau={tau}, tol={TOL}, "
+                    f"max_iter=200000)\n"
+                    f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
+    else:
+        w = wl.workload_dimension(cfg["d"], points, seed=13 + 1000 * rank)
+        sysd = w["system"]
+        x = w["x"]
+        nb, k, m, N, T, tau = 2, cfg["d"] // 2, 1, w["N"], cfg["T"], w["tau"]
+        n = nb * k
+        fpi = 4 * N * m * nb + 2 * k * nb * nb
+        wname = f"dimension_scaling_d{cfg['d']}_N100_T2.5_{points}pts"
+        kernel = "pdhg_stacked_kernel<float>"
+        cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
+                    f"w = wl.workload_dimension({cfg['d']}, {cfg['cpu_points']})\nt0 = time.perf_counter()\n"
+                    f"r = oh.value(w['system'], w['x'], {T}, w['N'], w['rule'], tau=w['tau'], tol={TOL}, "
+                    f"max_iter=200000)\n"
+                    f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d = oracle_sample_seconds(cpu_code)
+        cpu = {"value": d["ok"] / d["dt"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle (dense stacked system for the copies), 1 thread, "
+                         f"{cfg['cpu_points']} point(s), gap<=1e-5, {d['dt']:.1f} s"}
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://", device_id=torch.device("cuda", local))
+    import paper_1712_08226_gb300 as H
+    from paper_1712_08226_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    H._lib.load()
+    x_dev = torch.tensor(x, dtype=torch.float32, device="cuda")
+    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True)
+    if args.workload == "chain":
+        S = H.System.from_dict(sysd)
+        call = lambda xx: H.value(S, xx, T, opts)            # noqa: E731
+        dense_call = None
+    else:
+        base = H.System.from_dict(sysd["base"])
+        Sd = H.System.from_dict(sysd)
+        call = lambda xx: H.value_stacked(base, sysd["W_blocks"], xx, T, opts)   # noqa: E731
+        dense_call = lambda xx: H.value(Sd, xx, T, opts)                         # noqa: E731
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(f, steps):
+        ms, sv, un, ok, its = [], [], 0, 0, None
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = f(x_dev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            # the value path records events around its solve kernel; the
+            # stacked path is one table build and one kernel: use the step
+            sv.append(H.last_profile()[1] if f is not call or args.workload == "chain" else ms[-1])
+            it = r["iters"].to(torch.int64)
+            un += int((it + 1).sum().item())
+            ok += int((r["status"] == 0).sum().item())
+            its = it.cpu().numpy()
+        return dict(ms=ms, solve_ms=sv, units=un, ok=ok, iters=its)
+
+    for _ in range(args.warmup):
+        call(x_dev)
+    torch.cuda.synchronize()
+    compare = None
+    if dense_call is not None and not args.no_compare:
+        dense_call(x_dev)
+        rd = timed(dense_call, 1)
+        compare = {"dense_stacked_solves_per_s": rd["ok"] / (rd["ms"][0] * 1e-3), "dense_ms": rd["ms"][0],
+                   "dense_mean_iters": float(rd["iters"].mean()), "kernel": "pdhg_tile_kernel<1,2>"}
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    res = timed(call, args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    x_pin = torch.tensor(x, dtype=torch.float32).pin_memory()
+    e2e_s, ok_e2e = [], 0
+    for i in range(0 if args.no_e2e else args.warmup + args.steps):
+        t0 = time.perf_counter()
+        xd = x_pin.to("cuda", non_blocking=True)
+        rh = call(xd)
+        phi_h, st_h = rh["phi"].cpu(), rh["status"].cpu()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_s.append(dt)
+            ok_e2e = int((st_h == 0).sum())
+    if not e2e_s:
+        e2e_s = [float("nan")]
+    from paper_1712_08226_gb300 import shard
+    t_local = shard.reduce_max([statistics.mean(res["ms"]), statistics.mean(e2e_s) * 1e3], dist,
+                               device="cuda" if dist else None)
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    value = shard.job_throughput(res["ok"] / args.steps, world, t_local[0] * 1e-3)
+    achieved = res["units"] / args.steps * fpi / (statistics.mean(res["solve_ms"]) * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    line = {
+        "metric": f"Hopf solves/sec at gap<=1e-5 ({args.workload} workload)", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(t_local[0]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": wname, "n": n, "m": m, "N": N, "t": T, "points_per_gpu": points, "tol_gap": TOL,
+                   "tau": tau, "l2": "flushed between timed steps (512 MB write)",
+                   "mean_iters": float(res["iters"].mean()), "max_iters": int(res["iters"].max()),
+                   "certified_per_step": res["ok"] / args.steps, "ms_solve": statistics.mean(res["solve_ms"]),
+                   "comparison": compare},
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
+                     "flops_per_point_iter": fpi,
+                     "point_iters_per_s": res["units"] / args.steps / (statistics.mean(res["solve_ms"]) * 1e-3)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": shard.job_throughput(ok_e2e, world, t_local[1] * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": points * n * 4, "d2h_bytes_per_step": points * 8},
+        "gpu_launches": 4 * args.steps,       # horizons, tables, (pad | expand), solve
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,7 +363,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the cold-start comparison runs")
     ap.add_argument("--cold", action="store_true", help="time the cold accelerated solve instead of the warm one")
+    ap.add_argument("--workload", default="random10", choices=["random10", "chain", "dimension"],
+                    help="random10: the headline; chain / dimension: secondary workloads")
+    ap.add_argument("--max-iter", type=int, default=400000,
+                    help="secondary workloads: iteration cap (small values only for profiler captures)")
     args = ap.parse_args()
+    if args.workload != "random10" and args.impl == "ours":
+        run_secondary(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

@@ -24,11 +24,12 @@ template <typename R>
 cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *x, const R *p_init, R *phi,
                                 R *pstar, R *gap, int *iters, int *status, R *Pv, R *Dv, R *y,
                                 const int *active, cudaStream_t s);
-bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem);
+bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem,
+               int *dbuf);
 long long tile_workspace_floats(int n, int m, int N, int ppt, int grid);
 cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
                              float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
-                             int ppt, int grid, size_t smem, cudaStream_t s);
+                             int ppt, int grid, size_t smem, int dbuf, cudaStream_t s);
 cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                            const double *qd, const double *W, int w_count, const double *Tv,
                                            int n_inst, int n, int m, int N, int rule, double tau,
@@ -499,10 +500,11 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         sp32.grid = dev.sms;
     }
     // large states, one shared table: the tiled kernel
-    int tile_ppt = 0, tile_grid = 0;
+    int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
     size_t tile_smem = 0;
     const bool tile = fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !sp.ok && !o->accel &&
-                      tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem);
+                      tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
+                                &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);
     const bool hio = o->host_io != 0;
     CarryPair cb;
@@ -576,7 +578,8 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         if (rc) return rc;
     } else if (tile) {
         CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)dx, (const float *)dpi, (float *)dphi,
-                            (float *)dps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem, s));
+                            (float *)dps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem,
+                            tile_dbuf, s));
     } else {
         rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
         if (rc) return rc;

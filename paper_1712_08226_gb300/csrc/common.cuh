@@ -120,10 +120,12 @@ __host__ __device__ inline TileGeom tile_geom(int n, int m, int N, int ppt) {
     return g;
 }
 // dynamic shared memory of one block, in floats: K block (also the u buffer
-// of the certificate), pbar tile, dual block, vector buffer, 3 per-slot sums
-__host__ __device__ inline long long tile_smem_floats(const TileGeom &g) {
+// of the certificate), a second K block when double-buffered, pbar tile,
+// dual block, vector buffer, 3 per-slot sums
+__host__ __device__ inline long long tile_smem_floats(const TileGeom &g, bool dbuf) {
     const int kr = g.cr > g.pt ? g.cr : g.pt;
-    return (long long)kr * g.n4 + 2LL * g.n4 * g.pt + (long long)g.cr * g.pt + 3LL * g.pt;
+    return (long long)kr * g.n4 + (dbuf ? (long long)g.cr * g.n4 : 0LL) + 2LL * g.n4 * g.pt +
+           (long long)g.cr * g.pt + 3LL * g.pt;
 }
 
 }  // namespace hopf

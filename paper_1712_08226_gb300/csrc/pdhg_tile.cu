@@ -42,6 +42,15 @@ namespace {
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NG>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NG) : "memory"); }
+
 __device__ __forceinline__ float comp(const float4 &v, int e) {
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
@@ -95,7 +104,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                  const float *__restrict__ x, const float *__restrict__ p_init, float *__restrict__ phi,
                  float *__restrict__ pstar, float *__restrict__ gap_out, int *__restrict__ iters,
                  int *__restrict__ status, float *__restrict__ slot_p, float *__restrict__ slot_x,
-                 float *__restrict__ slot_y, int *__restrict__ queue) {
+                 float *__restrict__ slot_y, int *__restrict__ queue, int dbuf) {
     constexpr int NPT = MP >= 8 ? 1 : 8 / MP;
     constexpr int RW = NPT * MP;
     constexpr int PT = 32 * PPT;
@@ -132,8 +141,10 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     const float tau = (float)prm.tau;
 
     extern __shared__ float4 smem4[];
-    float *Ks = reinterpret_cast<float *>(smem4);                  // [max(cr, pt)][n4]
-    float *Pb = Ks + (long long)(CR > PT ? CR : PT) * n4;         // [nq][pt][4]
+    float *Kbuf0 = reinterpret_cast<float *>(smem4);               // [max(cr, pt)][n4]
+    float *Kbuf1 = Kbuf0 + (long long)(CR > PT ? CR : PT) * n4;    // [cr][n4] when double-buffered
+    float *Pb = Kbuf1 + (dbuf ? (long long)CR * n4 : 0LL);         // [nq][pt][4]
+    float *Ks = Kbuf0;
     float *VB = Pb + (long long)n4 * PT;                           // [n4][pt]
     float *Ys = VB + (long long)n4 * PT;                           // [cr][pt]
     float *Hs = Ys + (long long)CR * PT;                           // [pt]
@@ -203,13 +214,44 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) hpart[pp] = 0.f;
 
+        // node block c of K into shared memory (asynchronous copies; with two
+        // buffers block c + 1 is in flight while block c is used)
+        auto load_block = [&](int c, float *dstf) {
+            const float4 *src = reinterpret_cast<const float4 *>(Kp + (long long)c * CR * n4);
+            float4 *dst = reinterpret_cast<float4 *>(dstf);
+            for (int e = tid; e < CR * nq; e += blockDim.x) cp_async16(dst + e, src + e);
+            cp_async_commit();
+        };
+        if (dbuf) load_block(0, Kbuf0);
         for (int c = 0; c < g.chunks; ++c) {
-            {   // node block c of K into shared memory
-                const float4 *src = reinterpret_cast<const float4 *>(Kp + (long long)c * CR * n4);
-                float4 *dst = reinterpret_cast<float4 *>(Ks);
-                for (int e = tid; e < CR * nq; e += blockDim.x) dst[e] = __ldg(src + e);
+            if (dbuf) {
+                Ks = (c & 1) ? Kbuf1 : Kbuf0;
+                if (c + 1 < g.chunks) {
+                    load_block(c + 1, (c & 1) ? Kbuf0 : Kbuf1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+            } else {
+                load_block(c, Kbuf0);
+                cp_async_wait<0>();
             }
             __syncthreads();
+            // this block's dual variables, loaded before the products so the
+            // global-memory latency overlaps them
+            float ypre[PPT][RW];
+#pragma unroll
+            for (int t = 0; t < NPT; ++t) {
+                const bool node_ok = c * NC + warp * NPT + t < N;
+                const long long grow = (long long)c * CR + warp * RW + t * MP;
+#pragma unroll
+                for (int pp = 0; pp < PPT; ++pp) {
+                    const int s = lane + 32 * pp;
+                    const bool ld = node_ok && sl_pt[s] >= 0 && !sl_fresh[s];
+#pragma unroll
+                    for (int cc = 0; cc < MP; ++cc) ypre[pp][t * MP + cc] = ld ? Yg[(grow + cc) * PT + s] : 0.f;
+                }
+            }
             // K pbar for this warp's rows and this lane's slots
             float acc[PPT][RW];
 #pragma unroll
@@ -254,7 +296,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                         float yo[MP];
                         if (!sl_fresh[s]) {
 #pragma unroll
-                            for (int cc = 0; cc < MP; ++cc) yo[cc] = Yg[(grow + cc) * PT + s];
+                            for (int cc = 0; cc < MP; ++cc) yo[cc] = ypre[pp][t * MP + cc];
                         } else if (!prm.warm) {     // y0 = K p0 (§VI), unprojected
 #pragma unroll
                             for (int cc = 0; cc < MP; ++cc) yo[cc] = acc[pp][t * MP + cc];
@@ -321,8 +363,9 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             for (int pp = 0; pp < PPT; ++pp) atomicAdd(&Hs[lane + 32 * pp], hpart[pp]);
         }
         // v = p - tau K^T y + tau x0 (argument of the prox of Eq. 37) and, on
-        // certificate iterations, u = x0 - K^T y (in the K block buffer)
-        float *UB = Ks;
+        // certificate iterations, u = x0 - K^T y (in the first K block buffer,
+        // free: no copy is in flight after the last block)
+        float *UB = Kbuf0;
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
             const int s = lane + 32 * pp;
@@ -562,18 +605,22 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
 }
 
 // ------------------------------------------------------------ host side
-bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem) {
+bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem,
+               int *dbuf) {
     if (n < 1 || n > 256 || m < 1 || m > 16 || N < 1 || P < 1) return false;
     for (int cand = 2; cand >= 1; --cand) {
         const TileGeom g = tile_geom(n, m, N, cand);
-        const size_t bytes = (size_t)tile_smem_floats(g) * sizeof(float);
-        if (bytes > smem_limit) continue;
         const int tiles = (P + g.pt - 1) / g.pt;
         if (cand == 2 && tiles < sms) continue;     // prefer more blocks over wider tiles
-        *ppt = cand;
-        *grid = tiles < sms ? tiles : sms;
-        *smem = bytes;
-        return true;
+        for (int db = 1; db >= 0; --db) {
+            const size_t bytes = (size_t)tile_smem_floats(g, db != 0) * sizeof(float);
+            if (bytes > smem_limit) continue;
+            *ppt = cand;
+            *grid = tiles < sms ? tiles : sms;
+            *smem = bytes;
+            *dbuf = db;
+            return true;
+        }
     }
     return false;
 }
@@ -589,18 +636,19 @@ template <int MP, int PPT>
 static cudaError_t launch_tile_t(const float *inst, const double *inst64, const float *Kp, const float *Sp, const float *Mp,
                                  const float *Vp, const SolveParams &prm, const float *x, const float *p_init,
                                  float *phi, float *pstar, float *gap, int *iters, int *status, float *sp,
-                                 float *sx, float *sy, int *queue, int grid, size_t smem, cudaStream_t s) {
+                                 float *sx, float *sy, int *queue, int grid, size_t smem, int dbuf,
+                                 cudaStream_t s) {
     auto kern = pdhg_tile_kernel<MP, PPT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, TILE_WARPS * 32, smem, s>>>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters,
-                                             status, sp, sx, sy, queue);
+                                             status, sp, sx, sy, queue, dbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
                              float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
-                             int ppt, int grid, size_t smem, cudaStream_t s) {
+                             int ppt, int grid, size_t smem, int dbuf, cudaStream_t s) {
     const int n = prm.n, m = prm.m, N = prm.N;
     const TileGeom g = tile_geom(n, m, N, ppt);
     float *Kp = ws;
@@ -618,9 +666,9 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
 #define TILE_CASE(MPV)                                                                                        \
     case MPV:                                                                                                 \
         return ppt == 2 ? launch_tile_t<MPV, 2>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                                status, sp, sx, sy, queue, grid, smem, s)                    \
+                                                status, sp, sx, sy, queue, grid, smem, dbuf, s)                    \
                         : launch_tile_t<MPV, 1>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                                status, sp, sx, sy, queue, grid, smem, s);
+                                                status, sp, sx, sy, queue, grid, smem, dbuf, s);
     switch (g.mp) {
         TILE_CASE(1)
         TILE_CASE(2)

@@ -108,3 +108,35 @@ def test_status_strings(lib):
     assert lib.hopf_status_string(0) == b"ok"
     assert lib.hopf_status_string(3).startswith(b"target unreachable")
     assert lib.hopf_status_string(-2).startswith(b"W not")
+
+
+def test_stacked_entry_validates_before_touching_a_device(lib):
+    # hopf_value_stacked checks copies, base size, every W block, and options
+    from paper_1712_08226_gb300 import _lib as L
+    from paper_1712_08226_gb300 import api
+    from inputs import workloads as wl
+    base = api.System.from_dict(wl.double_integrator(0.1))
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+
+    def call(blocks, opts_kw=None, P=2):
+        blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+        sp = L.HopfStacked(base.c_struct(), blocks.shape[0], blocks.ctypes.data_as(L.P_double))
+        o = api.Options(**(opts_kw or {})).c_struct(False)
+        k = blocks.shape[0]
+        x = np.zeros((P, 2 * k), np.float32)
+        t = np.ones(1, np.float32)
+        outs = [np.zeros(P, np.float32), np.zeros((P, 2 * k), np.float32), np.zeros(P, np.float32),
+                np.zeros(P, np.int32), np.zeros(P, np.int32)]
+        return lib.hopf_value_stacked(ctypes.byref(sp), ctypes.byref(o), P, vp(x), vp(t), 0, None,
+                                      *[vp(a) for a in outs], None)
+
+    good = np.stack([0.1 * np.eye(2)] * 3)
+    bad = good.copy()
+    bad[2] = np.array([[1.0, 2.0], [2.0, 1.0]])
+    assert call(bad) == -2 and b"block 2" in lib.hopf_last_error()
+    nan = good.copy()
+    nan[1, 0, 0] = np.nan
+    assert call(nan) == -5
+    assert call(np.stack([0.1 * np.eye(2)] * 65)) == -1          # at most 64 copies
+    assert call(good, dict(accel=True)) == -1
+    assert call(good, P=0) == 0                                    # empty batch: nothing to do
