@@ -195,6 +195,9 @@ SECONDARY = {
     # 60 double-integrator samples sharing one control (d = 120): the structured
     # stacked-copy solve, with the dense stacked system as comparison
     "dimension": dict(points=16384, T=2.5, d=120, cpu_points=2),
+    # the first --systems of the 64 random systems (n = 4..128, m = ceil(n/8),
+    # 1000-4000 points each, t = 2, N = 256), solved one system per call
+    "ragged": dict(T=2.0, N=256, tau=0.15, cpu_points=1),
 }
 
 
@@ -215,8 +218,24 @@ def run_secondary(args):
         cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
                     f"x = wl.normal_points(3, {cfg['cpu_points']}, 200, 1.0)\nt0 = time.perf_counter()\n"
                     f"r = oh.value(wl.spring_chain(), x, {T}, {N}, oh.LEFT_RIEMANN, tau={tau}, tol={TOL}, "
-                    f"max_iter=200000)\n"
+                    f"max_iter=200000, accel={bool(args.accel)})\n"
                     f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
+    elif args.workload == "ragged":
+        wr = wl.workload_ragged()
+        items = wr["items"][:args.systems]
+        N, T, tau, m = cfg["N"], cfg["T"], cfg["tau"], None
+        n = max(it["system"]["A"].shape[0] for it in items)
+        points = sum(len(it["x"]) for it in items)
+        fpi = None
+        wname = f"ragged_random_systems_first{len(items)}_of_64_N256_t2_{points}pts"
+        kernel = "pdhg_tile_kernel (n > 16) / pdhg_small_kernel (n <= 16)"
+        s0 = items[0]["system"]
+        cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
+                    f"it = wl.workload_ragged()['items'][0]\nt0 = time.perf_counter()\n"
+                    f"r = oh.value(it['system'], it['x'][:{cfg['cpu_points']}], {T}, {N}, oh.LEFT_RIEMANN, "
+                    f"tau={tau}, tol={TOL}, max_iter=200000)\n"
+                    f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
+        x = None
     else:
         w = wl.workload_dimension(cfg["d"], points, seed=13 + 1000 * rank)
         sysd = w["system"]
@@ -250,8 +269,12 @@ def run_secondary(args):
     if dist:
         dist.barrier()
     H._lib.load()
+    accel = bool(args.accel)
+    if args.workload == "ragged":
+        run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel, N, T, tau)
+        return
     x_dev = torch.tensor(x, dtype=torch.float32, device="cuda")
-    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True)
+    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True, accel=accel)
     if args.workload == "chain":
         S = H.System.from_dict(sysd)
         call = lambda xx: H.value(S, xx, T, opts)            # noqa: E731
@@ -334,7 +357,8 @@ def run_secondary(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded)",
         "config": {"workload": wname, "n": n, "m": m, "N": N, "t": T, "points_per_gpu": points, "tol_gap": TOL,
-                   "tau": tau, "l2": "flushed between timed steps (512 MB write)",
+                   "tau": tau, "iteration": "accelerated (strongly convex G)" if accel else "Eq. 15 (theta = 1)",
+                   "l2": "flushed between timed steps (512 MB write)",
                    "mean_iters": float(res["iters"].mean()), "max_iters": int(res["iters"].max()),
                    "certified_per_step": res["ok"] / args.steps, "ms_solve": statistics.mean(res["solve_ms"]),
                    "comparison": compare},
@@ -352,6 +376,72 @@ def run_secondary(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel, N, T, tau):
+    """Secondary line for the ragged systems: one hopf_value call per system
+    per step (each with its own node table), timed together."""
+    import torch
+    xs = [torch.tensor(it["x"], dtype=torch.float32, device="cuda") for it in items]
+    systems = [H.System.from_dict(it["system"]) for it in items]
+    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        out = []
+        for S, xd in zip(systems, xs):
+            out.append(H.value(S, xd, T, opts))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, ok, flops, its = [], 0, 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        for S, r in zip(systems, rs):
+            it = r["iters"].to(torch.int64)
+            ok += int((r["status"] == 0).sum().item())
+            flops += float((it + 1).sum().item()) * flops_per_point_iter(S.n, S.m, N)
+            its.append(it.cpu().numpy())
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    t = statistics.mean(ms) * 1e-3
+    achieved = flops / args.steps / t / 1e12
+    props = torch.cuda.get_device_properties(0)
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    its = np.concatenate(its)
+    ns = [S.n for S in systems]
+    line = {
+        "metric": "Hopf solves/sec at gap<=1e-5 (ragged workload)", "value": ok / args.steps / t,
+        "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": wname, "systems": len(systems), "n_per_system": ns, "N": N, "t": T, "tau": tau,
+                   "tol_gap": TOL, "points": int(sum(len(x) for x in xs)), "mean_iters": float(its.mean()),
+                   "max_iters": int(its.max()), "certified_per_step": ok / args.steps,
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
+                     "timing": "whole step (tables + solves, systems in sequence)"},
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": 4 * len(systems) * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,8 +453,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the cold-start comparison runs")
     ap.add_argument("--cold", action="store_true", help="time the cold accelerated solve instead of the warm one")
-    ap.add_argument("--workload", default="random10", choices=["random10", "chain", "dimension"],
+    ap.add_argument("--systems", type=int, default=8, help="ragged workload: how many of the 64 systems")
+    ap.add_argument("--workload", default="random10", choices=["random10", "chain", "dimension", "ragged"],
                     help="random10: the headline; chain / dimension: secondary workloads")
+    ap.add_argument("--accel", action="store_true", help="secondary chain workload: accelerated steps")
     ap.add_argument("--max-iter", type=int, default=400000,
                     help="secondary workloads: iteration cap (small values only for profiler captures)")
     args = ap.parse_args()

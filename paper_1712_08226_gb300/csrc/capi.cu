@@ -502,7 +502,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     // large states, one shared table: the tiled kernel
     int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
     size_t tile_smem = 0;
-    const bool tile = fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !sp.ok && !o->accel &&
+    const bool tile = fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !sp.ok &&
                       tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
                                 &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);

@@ -56,7 +56,8 @@ __device__ __forceinline__ float comp(const float4 &v, int e) {
 }
 
 // one-off: zero-padded float32 copies of K ([chunks cr][n4], row i mp + c for
-// node i and control component c), and of the symmetric S, M, V ([n][n4])
+// node i and control component c), of the symmetric S, M, V and of the
+// eigenvectors U of M and their transpose ([n][n4] each, contiguous from Sp)
 __global__ void tile_pad_kernel(const float *__restrict__ inst, int n, int m, int N, TileGeom g,
                                 float *__restrict__ Kp, float *__restrict__ Sp, float *__restrict__ Mp,
                                 float *__restrict__ Vp) {
@@ -64,7 +65,7 @@ __global__ void tile_pad_kernel(const float *__restrict__ inst, int n, int m, in
     const long long nk = (long long)g.chunks * g.cr * g.n4;
     const long long nm = (long long)n * g.n4;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk + 3 * nm; e += stride) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nk + 5 * nm; e += stride) {
         if (e < nk) {
             const long long row = e / g.n4;
             const int j = (int)(e % g.n4);
@@ -76,9 +77,12 @@ __global__ void tile_pad_kernel(const float *__restrict__ inst, int n, int m, in
             const int which = (int)(f / nm);
             const long long r = f % nm;
             const int b = (int)(r / g.n4), a = (int)(r % g.n4);
-            const long long off = which == 0 ? L.S : (which == 1 ? L.M : L.V);
-            const float v = a < n ? inst[off + (long long)b * n + a] : 0.f;
-            (which == 0 ? Sp : (which == 1 ? Mp : Vp))[r] = v;
+            float v = 0.f;
+            if (a < n) {
+                if (which == 4) v = inst[L.U + (long long)a * n + b];           // U^T
+                else v = inst[(which == 0 ? L.S : which == 1 ? L.M : which == 2 ? L.V : L.U) + (long long)b * n + a];
+            }
+            Sp[(long long)which * nm + r] = v;
         }
     }
 }
@@ -137,8 +141,9 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         }
         return;
     }
-    const float sigma = sc[SC_SIGMA];
-    const float tau = (float)prm.tau;
+    const float gamma = sc[SC_GAMMA];
+    const float *lam = inst + L.lam;
+    const float *Up = Sp + 3LL * n * n4, *Utp = Sp + 4LL * n * n4;   // U and U^T, padded
 
     extern __shared__ float4 smem4[];
     float *Kbuf0 = reinterpret_cast<float *>(smem4);               // [max(cr, pt)][n4]
@@ -150,7 +155,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     float *Hs = Ys + (long long)CR * PT;                           // [pt]
     float *Qs = Hs + PT, *Ds = Qs + PT;
     __shared__ int sl_pt[PT], sl_cnt[PT], sl_fresh[PT], sl_done[PT];
-    __shared__ float sl_tol[PT];
+    __shared__ float sl_tol[PT], sl_tau[PT], sl_sig[PT];
     __shared__ int s_check, s_active, s_verify;
     __shared__ double red[TILE_WARPS];
 
@@ -167,6 +172,8 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         sl_fresh[tid] = 1;
         sl_done[tid] = 0;
         sl_tol[tid] = (float)prm.tol_gap;
+        sl_tau[tid] = (float)prm.tau;
+        sl_sig[tid] = sc[SC_SIGMA];
     }
     __syncthreads();
     for (int e = tid; e < n4 * PT; e += blockDim.x) {
@@ -309,6 +316,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                             }
                         }
                         float nu = 0.f;
+                        const float sigma = sl_sig[s];
 #pragma unroll
                         for (int cc = 0; cc < MP; ++cc) {
                             yn[cc] = fmaf(sigma, acc[pp][t * MP + cc], yo[cc]);
@@ -369,6 +377,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
             const int s = lane + 32 * pp;
+            const float tau = sl_tau[s];
 #pragma unroll
             for (int k = 0; k < NQW; ++k) {
                 const int q = warp + 8 * k;
@@ -535,12 +544,16 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         for (int pp = 0; pp < PPT; ++pp)
 #pragma unroll
             for (int k = 0; k < NQW; ++k) pn[pp][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // plain step: p_new = S v.  Accelerated step (tau changes every
+        // iteration): p_new = U diag(1 / (1 + tau lam / 2)) U^T v, the product
+        // U^T v going through the u buffer (free after the certificate).
+        const float *P1 = prm.accel ? Up : Sp;
 #pragma unroll
         for (int k = 0; k < NQW; ++k) {
             const int q = warp + 8 * k;
             if (q >= nq) break;
             for (int b = 0; b < n; ++b) {
-                const float4 s4 = __ldg(reinterpret_cast<const float4 *>(Sp + (long long)b * n4) + q);
+                const float4 s4 = __ldg(reinterpret_cast<const float4 *>(P1 + (long long)b * n4) + q);
 #pragma unroll
                 for (int pp = 0; pp < PPT; ++pp) {
                     const float v = VB[b * PT + lane + 32 * pp];
@@ -551,12 +564,51 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                 }
             }
         }
+        if (prm.accel) {
+            __syncthreads();                       // every product of v done before U^T v is stored
+#pragma unroll
+            for (int pp = 0; pp < PPT; ++pp) {
+                const int s = lane + 32 * pp;
+                const float ht = 0.5f * sl_tau[s];
+#pragma unroll
+                for (int k = 0; k < NQW; ++k) {
+                    const int q = warp + 8 * k;
+                    if (q < nq) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = 4 * q + e;
+                            UB[j * PT + s] = j < n ? comp(pn[pp][k], e) / fmaf(ht, __ldg(lam + j), 1.f) : 0.f;
+                        }
+                    }
+                    pn[pp][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < NQW; ++k) {
+                const int q = warp + 8 * k;
+                if (q >= nq) break;
+                for (int b = 0; b < n; ++b) {
+                    const float4 s4 = __ldg(reinterpret_cast<const float4 *>(Utp + (long long)b * n4) + q);
+#pragma unroll
+                    for (int pp = 0; pp < PPT; ++pp) {
+                        const float v = UB[b * PT + lane + 32 * pp];
+                        pn[pp][k].x = fmaf(s4.x, v, pn[pp][k].x);
+                        pn[pp][k].y = fmaf(s4.y, v, pn[pp][k].y);
+                        pn[pp][k].z = fmaf(s4.z, v, pn[pp][k].z);
+                        pn[pp][k].w = fmaf(s4.w, v, pn[pp][k].w);
+                    }
+                }
+            }
+        }
         __syncthreads();
         // p <- S v, pbar <- 2 p_new - p_old for the slots that go on
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
             const int s = lane + 32 * pp;
             if (sl_pt[s] < 0 || sl_done[s]) continue;
+            // theta = 1 (Eq. 15) or 1 / sqrt(1 + 2 gamma tau) (accelerated)
+            const float th = prm.accel ? rsqrtf(fmaf(2.f * gamma, sl_tau[s], 1.f)) : 1.f;
 #pragma unroll
             for (int k = 0; k < NQW; ++k) {
                 const int q = warp + 8 * k;
@@ -567,7 +619,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                         const float pnew = comp(pn[pp][k], e);
                         const float pold = ps[j * PT + s];
                         ps[j * PT + s] = pnew;
-                        pb_at(j, s) = fmaf(2.f, pnew, -pold);
+                        pb_at(j, s) = fmaf(th, pnew - pold, pnew);
                     }
                 }
             }
@@ -582,8 +634,15 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                 sl_cnt[s] = 0;
                 sl_fresh[s] = 1;
                 sl_tol[s] = (float)prm.tol_gap;
+                sl_tau[s] = (float)prm.tau;
+                sl_sig[s] = sc[SC_SIGMA];
             } else {
                 sl_fresh[s] = 0;
+                if (prm.accel && sl_pt[s] >= 0) {
+                    const float th = rsqrtf(fmaf(2.f * gamma, sl_tau[s], 1.f));
+                    sl_tau[s] *= th;
+                    sl_sig[s] /= th;
+                }
             }
         }
         __syncthreads();
@@ -628,7 +687,7 @@ bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt,
 // workspace floats: padded K, S, M, V; per-block p, x0 and dual buffers
 long long tile_workspace_floats(int n, int m, int N, int ppt, int grid) {
     const TileGeom g = tile_geom(n, m, N, ppt);
-    return (long long)g.chunks * g.cr * g.n4 + 3LL * n * g.n4 + 2LL * grid * g.n4 * g.pt +
+    return (long long)g.chunks * g.cr * g.n4 + 5LL * n * g.n4 + 2LL * grid * g.n4 * g.pt +
            (long long)grid * g.chunks * g.cr * g.pt + 16;
 }
 
@@ -655,7 +714,7 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
     float *Sp = Kp + (long long)g.chunks * g.cr * g.n4;
     float *Mp = Sp + (long long)n * g.n4;
     float *Vp = Mp + (long long)n * g.n4;
-    float *sp = Vp + (long long)n * g.n4;
+    float *sp = Vp + 3LL * n * g.n4;             // after V come U and U^T
     float *sx = sp + (long long)grid * g.n4 * g.pt;
     float *sy = sx + (long long)grid * g.n4 * g.pt;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);

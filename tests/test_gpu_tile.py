@@ -155,3 +155,23 @@ def test_structured_stacked_solve_matches_dense(H, which, prec):
     ref2 = np.array([oracle_phi(w["system"], w["x"][i:i + 1], Tp[i], w["N"], w["rule"], w["tau"],
                                 tol=1e-11 if prec == 64 else 1e-8)[0] for i in range(len(Tp))])
     assert rel_err(np_(r2["phi"]), ref2).max() <= tol
+
+
+@pytest.mark.parametrize("case", ["chain_box", "random_ball"])
+def test_tile_accelerated_against_oracle(H, case):
+    # the accelerated steps (strongly convex G, per-slot tau and sigma, prox
+    # through the eigen-decomposition of M) reach the oracle's value
+    if case == "chain_box":
+        sysd = wl.spring_chain(masses=20, actuators=10, radius_target=0.5)
+        x, T, N = wl.normal_points(5, 40, 40, 1.0), 3.0, 64
+    else:
+        sysd = wl.random_system(341, 36, 4)
+        x, T, N = wl.normal_points(342, 40, 36, 2.0), 1.5, 64
+    o = H.Options(N=N, tau=2.0, tol_gap=1e-5, max_iter=400000, accel=True)
+    r = H.value(H.System.from_dict(sysd), cuda(x), T, o)
+    assert np.all(r["status"].cpu().numpy() == 0)
+    from oracle import hopf as oh
+    idx = np.arange(0, 40, 8)
+    ref = oh.value(sysd, x[idx], T, N, wl.LEFT_RIEMANN, 2.0, tol=1e-8, max_iter=400000, accel=True)
+    assert np.all(ref["status"] == 0)
+    assert rel_err(np_(r["phi"])[idx], ref["phi"]).max() <= 1e-5
