@@ -207,7 +207,7 @@ def run_secondary(args):
     events on the launching stream, clocks sampled)."""
     cfg = SECONDARY[args.workload]
     rank, world, local = rank_env()
-    points = args.points if args.points != POINTS else cfg["points"]
+    points = args.points if args.points != POINTS else cfg.get("points", 0)
     if args.workload == "chain":
         sysd = wl.spring_chain()
         x = wl.normal_points(3 + 1000 * rank, points, 200, 1.0)

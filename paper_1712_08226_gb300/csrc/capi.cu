@@ -30,6 +30,10 @@ long long tile_workspace_floats(int n, int m, int N, int ppt, int grid);
 cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
                              float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
                              int ppt, int grid, size_t smem, int dbuf, cudaStream_t s);
+cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                       const double *qd, const double *W, const double *Tv, const int *active,
+                                       int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
+                                       double *out64, float *out32, double *scratch, int need_eig);
 cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                            const double *qd, const double *W, int w_count, const double *Tv,
                                            int n_inst, int n, int m, int N, int rule, double tau,
@@ -474,8 +478,8 @@ int launch_generic(const R *inst, const SolveParams &prm, const R *x, const R *p
 int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *o, const double *Tv,
                   const int *active, int n_inst, double *inst64, float *inst32, double *scratch, int grid,
                   cudaStream_t s) {
-    CU(launch_build_instances(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
-                              pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch));
+    CU(launch_build_instances_opt(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
+                                  pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch, o->accel));
     return HOPF_SUCCESS;
 }
 

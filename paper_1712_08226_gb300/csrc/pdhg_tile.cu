@@ -268,6 +268,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             {
                 const float4 *Kw = reinterpret_cast<const float4 *>(Ks) + (long long)warp * RW * nq;
                 const float4 *P4 = reinterpret_cast<const float4 *>(Pb);
+#pragma unroll 2
                 for (int q = 0; q < nq; ++q) {
                     float4 pv[PPT];
 #pragma unroll
@@ -344,6 +345,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             // K^T y over this node block: warp w, quads w, w + 8, ...
             {
                 const float4 *K4 = reinterpret_cast<const float4 *>(Ks);
+#pragma unroll 2
                 for (int r = 0; r < CR; ++r) {
                     float yv[PPT];
 #pragma unroll

@@ -23,7 +23,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                                        const double *__restrict__ Tv, const int *__restrict__ active,
                                        int n_inst, int n, int m, int N, int rule, double tau,
                                        double sigma_scale, double *out64, float *out32,
-                                       double *scratch, bool smem_scratch, int w_count) {
+                                       double *scratch, bool smem_scratch, int w_count, int need_eig) {
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     // scratch in shared memory when the launch provides it (small n), else global
     extern __shared__ double tsm[];
@@ -113,11 +113,18 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         } else {
             L2 = cta::lambda_max(C, n, v, u, red);
         }
-        // M = U diag(lam) U^T for the accelerated prox (I + tau M/2)^-1 = U diag(1/(1 + tau lam/2)) U^T
-        cta::copy(T2, Mo, n * n);
-        cta::sym_eig(T2, T1, v, n, red, rot);
-        cta::copy(o + L.U, T1, n * n);
-        cta::copy(o + L.lam, v, n);
+        // M = U diag(lam) U^T for the accelerated prox (I + tau M/2)^-1 =
+        // U diag(1/(1 + tau lam/2)) U^T; only the accelerated iteration uses it
+        if (need_eig) {
+            cta::copy(T2, Mo, n * n);
+            cta::sym_eig(T2, T1, v, n, red, rot);
+            cta::copy(o + L.U, T1, n * n);
+            cta::copy(o + L.lam, v, n);
+        } else {
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) o[L.U + e] = 0.0;
+            for (int e = threadIdx.x; e < n; e += blockDim.x) o[L.lam + e] = 0.0;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             double lmin = o[L.lam];
             for (int i = 1; i < n; ++i) lmin = fmin(lmin, o[L.lam + i]);
@@ -154,7 +161,22 @@ cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const 
     const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
-                                                                      tau, sigma_scale, out64, out32, scratch, in_smem, 1);
+                                                                      tau, sigma_scale, out64, out32, scratch, in_smem, 1,
+                                                                      1);
+    return cudaGetLastError();
+}
+
+// as launch_build_instances, with the eigen-decomposition of M (used only by
+// the accelerated iteration) optional
+cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
+                                       const double *qd, const double *W, const double *Tv, const int *active,
+                                       int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
+                                       double *out64, float *out32, double *scratch, int need_eig) {
+    const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
+    const bool in_smem = bytes <= 48 * 1024;
+    build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
+                                                                      tau, sigma_scale, out64, out32, scratch, in_smem, 1,
+                                                                      need_eig);
     return cudaGetLastError();
 }
 
@@ -167,7 +189,7 @@ cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, nullptr, n_inst, n, m, N,
                                                                       rule, tau, sigma_scale, out64, out32, scratch,
-                                                                      in_smem, w_count);
+                                                                      in_smem, w_count, 0);
     return cudaGetLastError();
 }
 
