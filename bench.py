@@ -275,7 +275,31 @@ def run_secondary(args):
         return
     x_dev = torch.tensor(x, dtype=torch.float32, device="cuda")
     opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True, accel=accel)
-    if args.workload == "chain":
+    warm_info = None
+    if args.workload == "chain" and args.warm:
+        # untimed set-up: label seeded training points with the GPU solver
+        # (certified ones only) and train the 200-256-256-200 network
+        from paper_1712_08226_gb300.warmstart import WarmStartNet, value_warm
+        S = H.System.from_dict(sysd)
+        t0 = time.perf_counter()
+        xtr = torch.tensor(wl.normal_points(4 + 1000 * rank, args.train_points, n, 1.0), dtype=torch.float32,
+                           device="cuda")
+        lab = H.value(S, xtr, T, H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=60000))
+        okm = lab["status"] == 0
+        xtr, ptr = xtr[okm].contiguous(), lab["p"][okm].contiguous()
+        torch.cuda.synchronize()
+        t_label = time.perf_counter() - t0
+        net = WarmStartNet(n, n, hidden=256, seed=0)
+        net.set_normalisation(xtr, ptr)
+        t0 = time.perf_counter()
+        hist = net.fit(xtr, ptr, epochs=args.train_epochs, batch=1024, lr=2e-3)
+        torch.cuda.synchronize()
+        warm_info = {"train_points": int(xtr.shape[0]), "label_s": round(t_label, 1), "epochs": args.train_epochs,
+                     "train_s": round(time.perf_counter() - t0, 1), "loss_first_epoch": hist[0],
+                     "loss_last_epoch": hist[-1], "network": "200-256-256-200 GELU, bf16 weights, fp32 accumulation"}
+        call = lambda xx: value_warm(S, xx, T, net, opts)     # noqa: E731
+        dense_call = None
+    elif args.workload == "chain":
         S = H.System.from_dict(sysd)
         call = lambda xx: H.value(S, xx, T, opts)            # noqa: E731
         dense_call = None
@@ -361,7 +385,7 @@ def run_secondary(args):
                    "l2": "flushed between timed steps (512 MB write)",
                    "mean_iters": float(res["iters"].mean()), "max_iters": int(res["iters"].max()),
                    "certified_per_step": res["ok"] / args.steps, "ms_solve": statistics.mean(res["solve_ms"]),
-                   "comparison": compare},
+                   "comparison": compare, "warm_start": warm_info},
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
@@ -370,7 +394,10 @@ def run_secondary(args):
         "cpu_baseline": cpu,
         "e2e": {"value": shard.job_throughput(ok_e2e, world, t_local[1] * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": points * n * 4, "d2h_bytes_per_step": points * 8},
-        "gpu_launches": 4 * args.steps,       # horizons, tables, (pad | expand), solve
+        # horizons, tables, (pad | expand), solve; the warm start adds the network
+        # (standardise + 3 tensor-core GEMMs), 3 ordering kernels, the fallback
+        # list and a second pad + solve
+        "gpu_launches": (14 if warm_info else 4) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -386,10 +413,21 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # systems overlap on the GPU: one stream per system slot (the library
+    # keeps one workspace per stream), joined before the end event
+    side = [torch.cuda.Stream() for _ in range(min(args.streams, len(systems)))]
+
     def step():
         out = []
-        for S, xd in zip(systems, xs):
-            out.append(H.value(S, xd, T, opts))
+        ev0 = torch.cuda.Event()
+        ev0.record(stream)
+        for i, (S, xd) in enumerate(zip(systems, xs)):
+            st = side[i % len(side)]
+            st.wait_event(ev0)
+            with torch.cuda.stream(st):
+                out.append(H.value(S, xd, T, opts, stream=st))
+        for st in side:
+            stream.wait_stream(st)
         return out
 
     for _ in range(args.warmup):
@@ -427,13 +465,14 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
         "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": wname, "systems": len(systems), "n_per_system": ns, "N": N, "t": T, "tau": tau,
-                   "tol_gap": TOL, "points": int(sum(len(x) for x in xs)), "mean_iters": float(its.mean()),
+                   "tol_gap": TOL, "points": int(sum(len(x) for x in xs)), "streams": len(side),
+                   "mean_iters": float(its.mean()),
                    "max_iters": int(its.max()), "certified_per_step": ok / args.steps,
                    "l2": "flushed between timed steps (512 MB write)"},
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz (max SM clock)",
-                     "timing": "whole step (tables + solves, systems in sequence)"},
+                     "timing": "whole step (tables + solves; systems overlap on the side streams)"},
         "cpu_baseline": cpu,
         "e2e": None,
         "gpu_launches": 4 * len(systems) * args.steps,
@@ -454,9 +493,13 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the cold-start comparison runs")
     ap.add_argument("--cold", action="store_true", help="time the cold accelerated solve instead of the warm one")
     ap.add_argument("--systems", type=int, default=8, help="ragged workload: how many of the 64 systems")
+    ap.add_argument("--streams", type=int, default=8, help="ragged workload: systems in flight at once")
     ap.add_argument("--workload", default="random10", choices=["random10", "chain", "dimension", "ragged"],
                     help="random10: the headline; chain / dimension: secondary workloads")
     ap.add_argument("--accel", action="store_true", help="secondary chain workload: accelerated steps")
+    ap.add_argument("--warm", action="store_true", help="secondary chain workload: learned warm start")
+    ap.add_argument("--train-points", type=int, default=8192, help="chain warm start: labelled training points")
+    ap.add_argument("--train-epochs", type=int, default=60, help="chain warm start: training epochs")
     ap.add_argument("--max-iter", type=int, default=400000,
                     help="secondary workloads: iteration cap (small values only for profiler captures)")
     args = ap.parse_args()

@@ -30,9 +30,12 @@
  *    stream).  hopf_value and hopf_trajectory do not synchronise the host
  *    unless host_io is set; hopf_time_to_reach reads one int32 per
  *    bisection step back to the host to know when every point has finished.
- *  - The library keeps a grow-only device workspace per device (released by
- *    hopf_release_workspace).  Concurrent calls from several host threads are
- *    serialised by an internal lock.
+ *  - The library keeps a grow-only device workspace per device and stream
+ *    (released by hopf_release_workspace): calls on one stream reuse it in
+ *    stream order, calls on different streams use different workspaces and
+ *    may overlap on the GPU (e.g. several systems at once).  Concurrent calls
+ *    from several host threads are serialised by an internal lock (the GPU
+ *    work they enqueue still runs asynchronously).
  *  - Return value: HOPF_SUCCESS (0) or a negative HOPF_E* code; the message
  *    of the last failure is available from hopf_last_error().  Per-point
  *    outcomes are reported separately in status[] (HOPF_OK, ...).
@@ -228,7 +231,8 @@ const char *hopf_status_string(int code);
 /* Message of the most recent failed call on this host thread ("" if none). */
 const char *hopf_last_error(void);
 
-/* Frees the library's device workspace on the current device. */
+/* Frees the library's device workspaces (every stream) on the current device;
+ * waits for the device first. */
 int hopf_release_workspace(void);
 
 /* Device time of the phases of the most recent hopf_value call made with

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -151,7 +152,9 @@ struct Workspace {
     void *ptr = nullptr;
     size_t size = 0;
 };
-std::vector<Workspace> g_ws;
+// one grow-only workspace per (device, stream): calls on one stream reuse it
+// in stream order; calls on different streams may run concurrently
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
 
 // events of the last profiled hopf_value call
@@ -212,14 +215,13 @@ struct Arena {
     }
 };
 
-int ensure_workspace(size_t bytes, void **out) {
+int ensure_workspace(size_t bytes, void **out, cudaStream_t stream) {
     int dev = 0;
     CU(cudaGetDevice(&dev));
-    if ((int)g_ws.size() <= dev) g_ws.resize(dev + 1);
-    Workspace &w = g_ws[dev];
+    Workspace &w = g_ws[std::make_pair(dev, stream)];
     if (w.size < bytes) {
         if (w.ptr) {
-            CU(cudaDeviceSynchronize());
+            CU(cudaStreamSynchronize(stream));
             CU(cudaFree(w.ptr));
             w.ptr = nullptr;
             w.size = 0;
@@ -543,7 +545,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     Arena meas(nullptr);
     plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
     void *base = nullptr;
-    rc = ensure_workspace(meas.off, &base);
+    rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
     plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
@@ -640,7 +642,7 @@ int stacked_impl(const hopf_stacked *sp, const hopf_opts *o, int P, const void *
     Arena meas(nullptr);
     plan(meas);
     void *base = nullptr;
-    rc = ensure_workspace(meas.off, &base);
+    rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
     plan(a);
@@ -726,7 +728,7 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     Arena meas(nullptr);
     plan(meas);
     void *base = nullptr;
-    rc = ensure_workspace(meas.off, &base);
+    rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
     plan(a);
@@ -845,7 +847,7 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     Arena meas(nullptr);
     plan(meas);
     void *base = nullptr;
-    rc = ensure_workspace(meas.off, &base);
+    rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
     plan(a);
@@ -902,10 +904,16 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         sp32 = plan_small(dev, n, m, N, P, 32);
         sp32.grid = dev.sms;
     }
+    // large states, one shared table: the tiled kernel (warm solve and fallback)
+    int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
+    size_t tile_smem = 0;
+    const bool tile = t_stride == 0 && !sp.ok &&
+                      tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
+                                &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);
     DevProblem d;
     double *Tv, *i64, *tsc;
-    float *i32, *phat, *msc, *y;
+    float *i32, *phat, *msc, *y, *tws;
     int *list, *cnt, *ctr, *ord, *obucket, *ocount, *ototal;
     CarryPair cb;
     const bool hio = o->host_io != 0;
@@ -933,13 +941,14 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         obucket = a.template take<int>(P);
         ocount = a.template take<int>(ORDER_BUCKETS);
         ototal = a.template take<int>(4);
-        y = sp.ok ? nullptr : a.template take<float>((size_t)P * N * m);
+        y = (sp.ok || tile) ? nullptr : a.template take<float>((size_t)P * N * m);
+        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
     };
     Arena meas(nullptr);
     plan(meas);
     void *base = nullptr;
-    rc = ensure_workspace(meas.off, &base);
+    rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
     plan(a);
@@ -974,6 +983,11 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         if (sp.ok)
             return run_small_two_phase(sp, sp32, m, i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, cb,
                                        o->park_iters, s);
+        if (tile) {
+            CU(launch_pdhg_tile(i32, i64, pp, dx, pinit, dphi, dps, dgap, dit, dst, tws, ctr, tile_ppt, tile_grid,
+                                tile_smem, tile_dbuf, s));
+            return HOPF_SUCCESS;
+        }
         return launch_generic<float>(i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
     };
     // hardest-first order of the warm solve; the hardest points (one wave of
@@ -1168,7 +1182,7 @@ int hopf_mlp_forward(const hopf_mlp *net, int B, const float *x, float *y, void 
     if (B == 0) return HOPF_SUCCESS;
     void *base = nullptr;
     const size_t fl = (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, false);
-    rc = ensure_workspace(sizeof(float) * fl + 256, &base);
+    rc = ensure_workspace(sizeof(float) * fl + 256, &base, (cudaStream_t)stream);
     if (rc) return rc;
     int *err = (int *)((char *)base + ((sizeof(float) * fl + 127) & ~(size_t)127));
     return net_predict(net, B, x, y, (float *)base, err, (cudaStream_t)stream);
@@ -1183,7 +1197,7 @@ int hopf_mlp_loss_grad(const hopf_mlp *net, int B, const float *x, const float *
     if (B < 1 || !x || !y || !loss || !grad) return fail(HOPF_EINVAL, "bad batch or null array");
     void *base = nullptr;
     rc = ensure_workspace(sizeof(float) * (size_t)mlp_scratch_floats(net->n_in, net->hidden, net->n_out, B, true),
-                          &base);
+                          &base, (cudaStream_t)stream);
     if (rc) return rc;
     CU(mlp_loss_grad(net->n_in, net->hidden, net->n_out, (const __nv_bfloat16 *)net->w_bf16, net->w, net->x_shift,
                      net->x_scale, net->y_shift, net->y_scale, B, x, y, loss, grad, (float *)base,
@@ -1266,10 +1280,18 @@ int hopf_release_workspace(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;
     CU(cudaGetDevice(&dev));
-    if ((int)g_ws.size() > dev && g_ws[dev].ptr) {
-        CU(cudaDeviceSynchronize());
-        CU(cudaFree(g_ws[dev].ptr));
-        g_ws[dev] = Workspace();
+    bool synced = false;
+    for (auto it = g_ws.begin(); it != g_ws.end();) {
+        if (it->first.first == dev) {
+            if (!synced) {
+                CU(cudaDeviceSynchronize());
+                synced = true;
+            }
+            if (it->second.ptr) CU(cudaFree(it->second.ptr));
+            it = g_ws.erase(it);
+        } else {
+            ++it;
+        }
     }
     return HOPF_SUCCESS;
 }

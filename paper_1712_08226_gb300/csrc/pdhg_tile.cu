@@ -164,10 +164,15 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     float *Yg = slot_y + (long long)blockIdx.x * g.chunks * CR * PT;  // [chunks cr][pt]
     auto pb_at = [&](int j, int s) -> float & { return Pb[((j >> 2) * PT + s) * 4 + (j & 3)]; };
 
+    // the queue walks points 0..P-1, or list[0 .. *list_count) when given
+    const int Pq = prm.list ? *prm.list_count : P;
+    auto take = [&]() -> int {
+        const int q = atomicAdd(queue, 1);
+        return q < Pq ? (prm.list ? prm.list[q] : q) : -1;
+    };
     // fill every slot from the queue
     if (tid < PT) {
-        const int k = atomicAdd(queue, 1);
-        sl_pt[tid] = k < P ? k : -1;
+        sl_pt[tid] = take();
         sl_cnt[tid] = 0;
         sl_fresh[tid] = 1;
         sl_done[tid] = 0;
@@ -631,8 +636,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         if (tid < PT) {
             const int s = tid;
             if (sl_done[s]) {
-                const int k = atomicAdd(queue, 1);
-                sl_pt[s] = k < P ? k : -1;
+                sl_pt[s] = take();
                 sl_cnt[s] = 0;
                 sl_fresh[s] = 1;
                 sl_tol[s] = (float)prm.tol_gap;

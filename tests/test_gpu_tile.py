@@ -175,3 +175,28 @@ def test_tile_accelerated_against_oracle(H, case):
     ref = oh.value(sysd, x[idx], T, N, wl.LEFT_RIEMANN, 2.0, tol=1e-8, max_iter=400000, accel=True)
     assert np.all(ref["status"] == 0)
     assert rel_err(np_(r["phi"])[idx], ref["phi"]).max() <= 1e-5
+
+
+def test_calls_on_two_streams_overlap_safely(H):
+    # one workspace per stream: two systems solved concurrently on two streams
+    # give the same results as the same calls one after the other
+    import torch
+    sysA, sysB = wl.random_system(501, 30, 4), wl.random_system(502, 44, 6)
+    xA, xB = wl.normal_points(503, 300, 30, 2.0), wl.normal_points(504, 300, 44, 2.0)
+    o = H.Options(N=64, tau=0.2, tol_gap=1e-5, max_iter=200000)
+    SA, SB = H.System.from_dict(sysA), H.System.from_dict(sysB)
+    ref = [H.value(SA, cuda(xA), 1.0, o), H.value(SB, cuda(xB), 1.0, o)]
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a_in, b_in = cuda(xA), cuda(xB)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        ra = H.value(SA, a_in, 1.0, o, stream=s1)
+    with torch.cuda.stream(s2):
+        rb = H.value(SB, b_in, 1.0, o, stream=s2)
+    torch.cuda.synchronize()
+    # (the certificate sums use shared-memory float atomics, so the last bits
+    # and the exact stopping iteration may differ between runs)
+    for r, rr in ((ra, ref[0]), (rb, ref[1])):
+        assert np.all(r["status"].cpu().numpy() == 0)
+        assert rel_err(np_(r["phi"]), np_(rr["phi"])).max() <= 2e-5
