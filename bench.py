@@ -481,6 +481,65 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
     print(json.dumps(line), flush=True)
 
 
+def run_trajectory(args):
+    """Secondary line: optimal control and state samples (Eq. 27, 33) for the
+    100-mass chain, 4,096 points, T = 10, S = 1,000 samples, from p of
+    2,000-iteration solves (p only selects the controls; the trajectory
+    kernel's work does not depend on it).  Metric: trajectories per second."""
+    rank, world, local = rank_env()
+    import torch
+    torch.cuda.set_device(local)
+    import paper_1712_08226_gb300 as H
+    from paper_1712_08226_gb300 import build
+    build.build()
+    H._lib.load()
+    P = args.points if args.points != POINTS else 4096
+    n, m, N, T, S = 200, 10, 512, 10.0, 1000
+    sysd = H.System.from_dict(wl.spring_chain())
+    x = torch.tensor(wl.normal_points(3 + 1000 * rank, P, n, 1.0), dtype=torch.float32, device="cuda")
+    r = H.value(sysd, x, T, H.Options(N=N, tau=0.5, tol_gap=TOL, max_iter=2000))
+    p = r["p"].contiguous()
+    Tv = torch.full((P,), T, dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    o = H.Options()
+    for _ in range(args.warmup):
+        H.trajectory(sysd, x, Tv, p, S, o)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = H.trajectory(sysd, x, Tv, p, S, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    t = statistics.mean(ms) * 1e-3
+    out_bytes = P * (S + 1) * (n + m) * 4
+    fma64 = P * S * (2.0 * n * n + 2.0 * n * m)          # lambda and x recurrences, control product
+    line = {
+        "metric": "optimal trajectories/sec (chain workload, 1,001 samples each)", "value": P / t,
+        "unit": "trajectories/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (recurrences), f32 (output)", "data": "synthetic (seeded)",
+        "config": {"workload": f"spring_chain_n200_m10_T10_S1000_{P}pts", "n": n, "m": m, "S": S, "T": T,
+                   "points": P, "output_bytes": out_bytes, "output_GBps": out_bytes / t / 1e9,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "p_source": "2,000-iteration value solves (not certified)"},
+        "roofline": {"bound": "alu", "kernel": "trajectory_kernel<float> (float64 recurrences)",
+                     "achieved": 2 * fma64 / t / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                     "frac": 2 * fma64 / t / 1e12 / 1.25, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 rate (not measured on this pool)",
+                     "hbm_write_frac": out_bytes / t / 1e9 / 6795.8},   # measured copy bandwidth
+        "cpu_baseline": None, "e2e": None, "gpu_launches": 3 * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,7 +553,8 @@ def main():
     ap.add_argument("--cold", action="store_true", help="time the cold accelerated solve instead of the warm one")
     ap.add_argument("--systems", type=int, default=8, help="ragged workload: how many of the 64 systems")
     ap.add_argument("--streams", type=int, default=8, help="ragged workload: systems in flight at once")
-    ap.add_argument("--workload", default="random10", choices=["random10", "chain", "dimension", "ragged"],
+    ap.add_argument("--workload", default="random10",
+                    choices=["random10", "chain", "dimension", "ragged", "trajectory"],
                     help="random10: the headline; chain / dimension: secondary workloads")
     ap.add_argument("--accel", action="store_true", help="secondary chain workload: accelerated steps")
     ap.add_argument("--warm", action="store_true", help="secondary chain workload: learned warm start")
@@ -503,6 +563,9 @@ def main():
     ap.add_argument("--max-iter", type=int, default=400000,
                     help="secondary workloads: iteration cap (small values only for profiler captures)")
     args = ap.parse_args()
+    if args.workload == "trajectory" and args.impl == "ours":
+        run_trajectory(args)
+        return
     if args.workload != "random10" and args.impl == "ours":
         run_secondary(args)
         return

@@ -73,7 +73,12 @@ cudaError_t launch_ttr_finish(int P, cudaStream_t s, const int *st, const int *f
 template <typename R>
 cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                               const double *qd, int n, int m, int ctrl_kind, int P, const R *x, const R *T,
-                              const R *pstar, int S, R *xt, R *ut, double *scratch);
+                              const R *pstar, int S, R *xt, R *ut, double *scratch, const double *Eh_sh,
+                              const double *G_sh);
+template <typename R>
+cudaError_t launch_traj_minmax(int P, const R *T, double *out, cudaStream_t s);
+cudaError_t launch_traj_shared_expm(int threads, const double *A, int n, int S, const double *TT, double *Eh,
+                                    double *G, double *scratch, cudaStream_t s);
 long long mlp_param_count(int n_in, int h, int n_out);
 long long mlp_scratch_floats(int n_in, int h, int n_out, int B, bool train);
 cudaError_t mlp_forward(int n_in, int h, int n_out, const __nv_bfloat16 *wb, const float *w, const float *x_shift,
@@ -833,11 +838,13 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     const int grid = std::max(1, std::min(P, 4 * dev.sms));
     const long long per = 5LL * n * n + 4LL * n + 4LL * n * m + 48;
     DevProblem d;
-    double *sc;
+    double *sc, *shared, *mm;
     R *dx, *dT, *dps, *dxt, *dut;
     auto plan = [&](Arena &a) {
         d = take_problem(a, n, m);
         sc = a.template take<double>((size_t)grid * per);
+        shared = a.template take<double>(4LL * n * n + 16);   // e^{hA}, e^{-hA}, expm scratch
+        mm = a.template take<double>(2);
         dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
         dT = hio ? a.template take<R>(P) : (R *)T_;
         dps = hio ? a.template take<R>((size_t)P * n) : (R *)ps_;
@@ -858,8 +865,21 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
         CU(cudaMemcpyAsync(dT, T_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(dps, ps_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
     }
+    // one horizon for the whole batch (the common case): the step
+    // exponentials are computed once instead of once per point
+    double tmm[2] = {0.0, 1.0};
+    CU(launch_traj_minmax<R>(P, dT, mm, s));
+    CU(cudaMemcpyAsync(tmm, mm, sizeof tmm, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const double *Eh_sh = nullptr, *G_sh = nullptr;
+    if (tmm[0] == tmm[1]) {
+        double *Eh = shared, *G = shared + (long long)n * n;
+        CU(launch_traj_shared_expm(table_threads(n), d.A, n, S, mm, Eh, G, shared + 2LL * n * n, s));
+        Eh_sh = Eh;
+        G_sh = G;
+    }
     CU(launch_trajectory<R>(grid, table_threads(n), s, d.A, d.B, d.q, n, m, pr->ctrl_kind, P, dx, dT, dps, S,
-                            dxt, dut, sc));
+                            dxt, dut, sc, Eh_sh, G_sh));
     if (hio) {
         CU(cudaMemcpyAsync(xt_, dxt, sizeof(R) * P * (S + 1) * n, cudaMemcpyDeviceToHost, s));
         CU(cudaMemcpyAsync(ut_, dut, sizeof(R) * P * (S + 1) * m, cudaMemcpyDeviceToHost, s));
@@ -969,13 +989,19 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         g_prof.valid = false;
         CU(cudaEventRecord(g_prof.ev[0], s));
     }
-    CU(launch_horizons(n_inst, s, dt, true, Tv));
-    rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
+    // the node table (side stream) and the network's prediction of p* with
+    // the hardest-first ordering (caller's stream) are independent: overlap
+    Side *tsd = nullptr;
+    rc = side_stream(dev.id, &tsd);
     if (rc) return rc;
-    // prediction of p* from x
+    CU(cudaEventRecord(tsd->fork, s));
+    CU(cudaStreamWaitEvent(tsd->stream, tsd->fork, 0));
+    CU(launch_horizons(n_inst, tsd->stream, dt, true, Tv));
+    rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, tsd->stream);
+    if (rc) return rc;
+    CU(cudaEventRecord(tsd->join, tsd->stream));
     rc = net_predict(net, P, dx, phat, msc, ctr + 3, s);
     if (rc) return rc;
-    if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     SolveParams prm;
     fill_params(prm, pr, o, P);
     prm.inst_stride = t_stride ? 1 : 0;
@@ -1000,6 +1026,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     order_scan_kernel<<<1, 32, 0, s>>>(P, n_hard, ocount, ototal);
     order_scatter_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, obucket, ocount, ord);
     CU(cudaGetLastError());
+    CU(cudaStreamWaitEvent(s, tsd->join, 0));
+    if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     // warm solve, capped at max_iter_warm
     SolveParams pw = prm;
     pw.warm = 1;

@@ -193,16 +193,24 @@ __global__ void trajectory_kernel(const double *__restrict__ A, const double *__
                                   const double *__restrict__ qd, int n, int m, int ctrl_kind, int P,
                                   const R *__restrict__ x, const R *__restrict__ T,
                                   const R *__restrict__ pstar, int S, R *__restrict__ xt,
-                                  R *__restrict__ ut, double *scratch) {
+                                  R *__restrict__ ut, double *scratch, const double *Eh_sh,
+                                  const double *G_sh) {
     double *sc = scratch + (long long)blockIdx.x * (5LL * n * n + 4LL * n + 4LL * n * m + 48);
     double *X = sc, *T1 = X + n * n, *Eh = T1 + n * n, *G = Eh + n * n, *BQ = G + n * n;
+    // one horizon for every point: e^{hA} and e^{-hA} computed once, shared
+    if (Eh_sh) {
+        Eh = const_cast<double *>(Eh_sh);
+        G = const_cast<double *>(G_sh);
+    }
     double *xs = BQ + n * m, *lam = xs + n, *tmp = lam + n, *tmp2 = tmp + n, *gv = tmp2 + n;
     double *red = gv + 2 * n * m;   // >= 8 doubles
     for (int k = blockIdx.x; k < P; k += gridDim.x) {
         const double Tk = (double)T[k];
         const double h = Tk / (double)S;
-        cta::expm(Eh, A, h, n, X, T1, red);     // e^{hA}
-        cta::expm(G, A, -h, n, X, T1, red);     // e^{-hA}
+        if (!Eh_sh) {
+            cta::expm(Eh, A, h, n, X, T1, red);     // e^{hA}
+            cta::expm(G, A, -h, n, X, T1, red);     // e^{-hA}
+        }
         for (int e = threadIdx.x; e < n * m; e += blockDim.x) BQ[e] = B[e] * qd[e % m];
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             xs[j] = (double)x[(long long)k * n + j];
@@ -307,11 +315,60 @@ cudaError_t launch_ttr_finish(int P, cudaStream_t s, const int *st, const int *f
     return cudaGetLastError();
 }
 
+// smallest and largest horizon of the batch (one block)
+template <typename R>
+__global__ void traj_minmax_kernel(int P, const R *__restrict__ T, double *out) {
+    __shared__ double lo[256], hi[256];
+    double a = 1e300, b = -1e300;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        const double t = (double)T[k];
+        a = fmin(a, t);
+        b = fmax(b, t);
+    }
+    lo[threadIdx.x] = a;
+    hi[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            lo[threadIdx.x] = fmin(lo[threadIdx.x], lo[threadIdx.x + w]);
+            hi[threadIdx.x] = fmax(hi[threadIdx.x], hi[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = lo[0];
+        out[1] = hi[0];
+    }
+}
+
+// e^{hA} and e^{-hA} for the shared horizon T (h = T / S), one block
+__global__ void traj_shared_expm_kernel(const double *__restrict__ A, int n, int S, const double *TT,
+                                        double *Eh, double *G, double *scratch) {
+    double *X = scratch, *T1 = X + n * n, *red = T1 + n * n;
+    const double h = TT[0] / (double)S;
+    cta::expm(Eh, A, h, n, X, T1, red);
+    cta::expm(G, A, -h, n, X, T1, red);
+}
+
+template <typename R>
+cudaError_t launch_traj_minmax(int P, const R *T, double *out, cudaStream_t s) {
+    traj_minmax_kernel<R><<<1, 256, 0, s>>>(P, T, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traj_shared_expm(int threads, const double *A, int n, int S, const double *TT, double *Eh,
+                                    double *G, double *scratch, cudaStream_t s) {
+    traj_shared_expm_kernel<<<1, threads, 0, s>>>(A, n, S, TT, Eh, G, scratch);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                               const double *qd, int n, int m, int ctrl_kind, int P, const R *x, const R *T,
-                              const R *pstar, int S, R *xt, R *ut, double *scratch) {
-    trajectory_kernel<R><<<grid, threads, 0, s>>>(A, B, qd, n, m, ctrl_kind, P, x, T, pstar, S, xt, ut, scratch);
+                              const R *pstar, int S, R *xt, R *ut, double *scratch, const double *Eh_sh,
+                              const double *G_sh) {
+    trajectory_kernel<R><<<grid, threads, 0, s>>>(A, B, qd, n, m, ctrl_kind, P, x, T, pstar, S, xt, ut, scratch,
+                                                  Eh_sh, G_sh);
     return cudaGetLastError();
 }
 
@@ -330,7 +387,9 @@ cudaError_t launch_trajectory(int grid, int threads, cudaStream_t s, const doubl
                                               const double *, R *, int *);                                \
     template cudaError_t launch_trajectory<R>(int, int, cudaStream_t, const double *, const double *,     \
                                               const double *, int, int, int, int, const R *, const R *,   \
-                                              const R *, int, R *, R *, double *);
+                                              const R *, int, R *, R *, double *, const double *,         \
+                                              const double *);                                            \
+    template cudaError_t launch_traj_minmax<R>(int, const R *, double *, cudaStream_t);
 HOPF_TTR_INST(float)
 HOPF_TTR_INST(double)
 

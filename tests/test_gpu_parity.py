@@ -391,3 +391,24 @@ def test_unscented_time_to_reach_fp32_against_oracle(H):
     assert np.all(np.isin(r["status"].cpu().numpy(), (0, 4))), r["status"]
     Tg = np.array(g["T"])
     assert np.all(np.abs(np_(r["T"]) - Tg) <= 1e-4 * Tg), (np_(r["T"]), Tg)
+
+
+def test_trajectory_shared_horizon_matches_per_point(H):
+    # one horizon for the batch takes the shared-exponential path; the same
+    # points with the horizon nudged on one of them take the per-point path
+    import torch
+    from oracle import hopf as oh
+    g = gold("random10_values.json")
+    w = wl.workload_random10(6)
+    sysd = H.System.from_dict(w["system"])
+    x = cuda(w["x"], torch.float64)
+    p = cuda(np.array(g["p"][:6]), torch.float64)
+    S = 100
+    o = H.Options(precision=H.FP64)
+    shared = H.trajectory(sysd, x, cuda(np.full(6, 2.0), torch.float64), p, S, o)
+    Tp = np.full(6, 2.0)
+    Tp[5] = 2.0 + 1e-9
+    per = H.trajectory(sysd, x, cuda(Tp, torch.float64), p, S, o)
+    assert torch.equal(shared["x"][:5], per["x"][:5]) and torch.equal(shared["u"][:5], per["u"][:5])
+    xs, us = oh.trajectory(w["system"], w["x"][2], 2.0, np.array(g["p"][2]), S)
+    assert np.max(np.abs(np_(shared["x"])[2] - xs)) <= 1e-6

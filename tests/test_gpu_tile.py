@@ -200,3 +200,24 @@ def test_calls_on_two_streams_overlap_safely(H):
     for r, rr in ((ra, ref[0]), (rb, ref[1])):
         assert np.all(r["status"].cpu().numpy() == 0)
         assert rel_err(np_(r["phi"]), np_(rr["phi"])).max() <= 2e-5
+
+
+def test_tile_warm_start_path_and_fallback_list(H):
+    # value_warm on a large state runs the tiled kernel twice: the warm solve
+    # from the network's prediction (capped), then a cold solve of the listed
+    # points it left uncertified.  An untrained network and a tiny cap send
+    # most points down the fallback; every value must still match a cold solve.
+    import torch
+    from paper_1712_08226_gb300.warmstart import WarmStartNet, value_warm
+    sysd = wl.random_system(601, 40, 5)
+    x = cuda(wl.normal_points(602, 300, 40, 2.0))
+    S = H.System.from_dict(sysd)
+    o = H.Options(N=64, tau=0.2, tol_gap=1e-5, max_iter=200000)
+    cold = H.value(S, x, 1.0, o)
+    net = WarmStartNet(40, 40, hidden=64, seed=3)
+    net.set_normalisation(x, cold["p"])
+    w = value_warm(S, x, 1.0, net, o, max_iter_warm=40)
+    torch.cuda.synchronize()
+    assert int(w["n_fallback"].item()) > 0
+    assert np.all(w["status"].cpu().numpy() == 0)
+    assert rel_err(np_(w["phi"]), np_(cold["phi"])).max() <= 2e-5
