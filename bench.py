@@ -483,7 +483,7 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
 
 def run_chain_ttr(args):
     """Secondary line: minimum time to reach for the 100-mass chain (§IV),
-    bisection or (--newton) the Newton hybrid on [0, t_max = 40] with per-point
+    bisection or (--newton) the Newton hybrid on [0, --t-max] with per-point
     node tables (N = 512, float32 solves to gap 1e-5, tol_T 1e-5)."""
     rank, world, local = rank_env()
     import torch
@@ -496,7 +496,7 @@ def run_chain_ttr(args):
     n, N = 200, 512
     sysd = H.System.from_dict(wl.spring_chain())
     x = torch.tensor(wl.normal_points(3 + 1000 * rank, P, n, 1.0), dtype=torch.float32, device="cuda")
-    o = H.Options(N=N, tau=0.5, tol_gap=TOL, t_max=40.0, tol_T=1e-5, max_iter=args.max_iter, newton=args.newton)
+    o = H.Options(N=N, tau=0.5, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5, max_iter=args.max_iter, newton=args.newton)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         H.time_to_reach(sysd, x, o)
@@ -521,8 +521,8 @@ def run_chain_ttr(args):
         "metric": "time-to-reach solves/sec (chain workload)", "value": ok / args.steps / t, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax40_N512_{P}pts", "n": n, "m": 10, "N": N,
-                   "t_max": 40.0, "tol_gap": TOL, "tol_T": 1e-5, "points": P,
+        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax{args.t_max:g}_N512_{P}pts", "n": n, "m": 10, "N": N,
+                   "t_max": args.t_max, "tol_gap": TOL, "tol_T": 1e-5, "points": P,
                    "search": "newton hybrid" if args.newton else "certified bisection", "rounds": steps,
                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(r["status"].cpu().numpy(),
                                                                             return_counts=True))},
@@ -614,6 +614,7 @@ def main():
     ap.add_argument("--accel", action="store_true", help="secondary chain workload: accelerated steps")
     ap.add_argument("--warm", action="store_true", help="secondary chain workload: learned warm start")
     ap.add_argument("--newton", action="store_true", help="chain_ttr workload: Newton hybrid instead of bisection")
+    ap.add_argument("--t-max", type=float, default=40.0, help="chain_ttr workload: upper end of the bracket")
     ap.add_argument("--train-points", type=int, default=8192, help="chain warm start: labelled training points")
     ap.add_argument("--train-epochs", type=int, default=60, help="chain warm start: training epochs")
     ap.add_argument("--max-iter", type=int, default=400000,

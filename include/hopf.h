@@ -321,9 +321,9 @@ int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int
  *
  * The paper has no counterpart; this is a deployment variant.  Some callers
  * must not allocate at solve time: a hard real-time control loop (a device
- * allocation can synchronise the whole device and has no time bound), code
- * that runs while a CUDA graph is being captured (allocation calls are not
- * allowed there), or a process whose memory footprint is fixed after start-up.
+ * allocation can synchronise the whole device and has no time bound), or a
+ * process whose memory footprint is fixed after start-up (for instance one
+ * sharing the GPU under a fixed memory quota).
  * This entry point takes all of its scratch (a copy of A, B, Q and W, the node
  * tables, and each point's dual variable) from one static device array of
  * HOPF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until

@@ -3,9 +3,9 @@
 //
 // Some callers cannot call cudaMalloc (or any allocator) at solve time: a
 // control loop with a hard real-time budget, where an allocation may block
-// on a device-wide synchronisation; code that runs while a CUDA graph is
-// being captured, where allocation calls are not allowed; or a host process
-// that is forbidden to grow its memory footprint after start-up.  This entry
+// on a device-wide synchronisation, or a host process that is forbidden to
+// grow its memory footprint after start-up (for instance one sharing the GPU
+// under a fixed memory quota).  This entry
 // point serves them.  It runs the general primal-dual kernel (the one that
 // keeps each point's dual variable in global scratch) with every byte of
 // scratch taken from one file-scope device array of fixed size

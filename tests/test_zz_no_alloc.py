@@ -1,7 +1,7 @@
 """hopf_value_noalloc: the value solve for callers that cannot allocate.
 
-Real-time control loops, code running under CUDA-graph capture and processes
-with a fixed memory footprint cannot call cudaMalloc at solve time; this entry
+Real-time control loops and processes with a fixed memory footprint cannot
+call cudaMalloc at solve time; this entry
 point takes its scratch from a static device array instead.  The test calls it
 through the C ABI twice in a row (the array keeps the first call's contents)
 and checks each result against hopf_value within the value tolerance of the
