@@ -254,8 +254,9 @@ def run_secondary(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         d = oracle_sample_seconds(cpu_code)
         cpu = {"value": d["ok"] / d["dt"], "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle (dense stacked system for the copies), 1 thread, "
-                         f"{cfg['cpu_points']} point(s), gap<=1e-5, {d['dt']:.1f} s"}
+               "sample": f"FP64 numpy oracle{' (dense stacked system)' if args.workload == 'dimension' else ''}, "
+                         f"1 thread, {cfg['cpu_points']} point(s) of the workload"
+                         f"{' (first system)' if args.workload == 'ragged' else ''}, gap<=1e-5, {d['dt']:.1f} s"}
     import torch
     torch.cuda.set_device(local)
     dist = None
