@@ -28,9 +28,11 @@ cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *
 bool tile_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *ppt, int *grid, size_t *smem,
                int *dbuf);
 long long tile_workspace_floats(int n, int m, int N, int ppt, int grid);
-cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
-                             float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
-                             int ppt, int grid, size_t smem, int dbuf, cudaStream_t s);
+cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x,
+                             const float *p_init, float *phi, float *pstar, float *gap, int *iters, int *status,
+                             float *ws, int *queue, int ppt, int grid, size_t smem, int dbuf, float *carry_st,
+                             int *carry_list, cudaStream_t s);
+long long tile_carry_floats(int n, int m, int N, int ppt, int P);
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
@@ -522,7 +524,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
 
     auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
                     R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
-                    int *&ctr, float *&tws) {
+                    int *&ctr, float *&tws, float *&tcs, int *&tcl) {
         d = take_problem(a, n, m);
         Tv = a.template take<double>(n_inst);
         i64 = a.template take<double>((size_t)n_inst * L.stride);
@@ -539,6 +541,8 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         y = (sp.ok || tile) ? nullptr : a.template take<R>((size_t)P * N * m);
         ctr = a.template take<int>(4);
         tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
+        tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
     };
     DevProblem d;
@@ -546,14 +550,15 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     float *i32;
     R *dx, *dt, *dpi, *dphi, *dps, *dgap, *y;
     int *dit, *dst, *ctr;
-    float *tws;
+    float *tws, *tcs;
+    int *tcl;
     Arena meas(nullptr);
-    plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
+    plan(meas, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws, tcs, tcl);
     void *base = nullptr;
     rc = ensure_workspace(meas.off, &base, s);
     if (rc) return rc;
     Arena a(base);
-    plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws);
+    plan(a, d, Tv, i64, i32, tsc, dx, dt, dpi, dphi, dps, dgap, dit, dst, y, ctr, tws, tcs, tcl);
 
     rc = upload_problem(d, pr, s);
     if (rc) return rc;
@@ -590,7 +595,7 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     } else if (tile) {
         CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)dx, (const float *)dpi, (float *)dphi,
                             (float *)dps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem,
-                            tile_dbuf, s));
+                            tile_dbuf, tcs, tcl, s));
     } else {
         rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
         if (rc) return rc;
@@ -933,7 +938,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     const int tgrid = table_grid(dev, n_inst);
     DevProblem d;
     double *Tv, *i64, *tsc;
-    float *i32, *phat, *msc, *y, *tws;
+    float *i32, *phat, *msc, *y, *tws, *tcs;
+    int *tcl;
     int *list, *cnt, *ctr, *ord, *obucket, *ocount, *ototal;
     CarryPair cb;
     const bool hio = o->host_io != 0;
@@ -963,6 +969,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         ototal = a.template take<int>(4);
         y = (sp.ok || tile) ? nullptr : a.template take<float>((size_t)P * N * m);
         tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
+        tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
     };
     Arena meas(nullptr);
@@ -1011,7 +1019,7 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
                                        o->park_iters, s);
         if (tile) {
             CU(launch_pdhg_tile(i32, i64, pp, dx, pinit, dphi, dps, dgap, dit, dst, tws, ctr, tile_ppt, tile_grid,
-                                tile_smem, tile_dbuf, s));
+                                tile_smem, tile_dbuf, tcs, tcl, s));
             return HOPF_SUCCESS;
         }
         return launch_generic<float>(i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);

@@ -156,7 +156,8 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     float *Qs = Hs + PT, *Ds = Qs + PT;
     __shared__ int sl_pt[PT], sl_cnt[PT], sl_fresh[PT], sl_done[PT];
     __shared__ float sl_tol[PT], sl_tau[PT], sl_sig[PT];
-    __shared__ int s_check, s_active, s_verify;
+    __shared__ int s_check, s_active, s_verify, s_park;
+    __shared__ int sl_park[PT];
     __shared__ double red[TILE_WARPS];
 
     float *ps = slot_p + (long long)blockIdx.x * n4 * PT;          // [n4][pt]
@@ -666,6 +667,282 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             pb_at(j, s) = pv;
         }
         __syncthreads();
+        // drain: with the queue empty, a block down to a quarter of its slots
+        // costs as much per iteration as a full one.  It parks the points it
+        // still holds (pbar, p, step sizes, counts; the dual rows stay in this
+        // block's buffer) for the one-block-per-point tail kernel and leaves.
+        if (prm.carry_cap > 0) {
+            if (tid == 0) {
+                int act = 0, fresh = 0;
+                for (int s = 0; s < PT; ++s)
+                    if (sl_pt[s] >= 0) {
+                        ++act;
+                        fresh |= sl_fresh[s];
+                    }
+                const int q = *reinterpret_cast<volatile int *>(queue);
+                s_park = (act > 0 && !fresh && q >= Pq && 4 * act <= PT) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_park) {
+                const int CW = 2 * n4 + 4;
+                if (tid < PT) {
+                    const int s = tid;
+                    sl_park[s] = -1;
+                    if (sl_pt[s] >= 0) {
+                        const int e = atomicAdd(prm.out_count, 1);
+                        sl_park[s] = e;
+                        prm.out_list[2 * e] = sl_pt[s];
+                        prm.out_list[2 * e + 1] = blockIdx.x * PT + s;
+                        float *st = prm.out_st + (long long)e * CW + 2 * n4;
+                        st[0] = sl_tau[s];
+                        st[1] = sl_sig[s];
+                        st[2] = (float)sl_cnt[s];
+                        st[3] = sl_tol[s];
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < n4 * PT; e += blockDim.x) {
+                    const int j = e / PT, s = e % PT;
+                    const int slot = sl_park[s];
+                    if (slot < 0) continue;
+                    prm.out_st[(long long)slot * CW + j] = pb_at(j, s);
+                    prm.out_st[(long long)slot * CW + n4 + j] = ps[j * PT + s];
+                }
+                return;
+            }
+        }
+    }
+}
+
+// Tail of the tiled solve: one 256-thread block per parked point, the same
+// iteration (Eq. 15 or the accelerated steps) with the node table read from
+// L2 (the padded float32 copy the tiled kernel used) instead of shared memory.
+// A point alone on an SM then needs about 2 x (rows x n4 x 4 B) of L2 reads
+// per iteration instead of a whole tile's arithmetic.  Its dual variables
+// come from the tiled kernel's per-block buffer and stay in shared memory;
+// the certificate and the float64 re-certification are the tiled kernel's.
+__global__ void __launch_bounds__(256)
+pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__ inst64,
+                      const float *__restrict__ Kp, const float *__restrict__ Sp, SolveParams prm, int ppt,
+                      const float *__restrict__ x, float *__restrict__ phi, float *__restrict__ pstar,
+                      float *__restrict__ gap_out, int *__restrict__ iters, int *__restrict__ status,
+                      const float *__restrict__ slot_y, int *__restrict__ queue2) {
+    const int n = prm.n, m = prm.m, N = prm.N;
+    const TileGeom g = tile_geom(n, m, N, ppt);
+    const int n4 = g.n4, nq = g.nq, MPd = g.mp, PT = g.pt;
+    const int G = g.chunks * g.cr;                    // padded rows of the table
+    const int CW = 2 * n4 + 4;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    const float *wv = inst + L.w;
+    const float gamma = inst[L.sc + SC_GAMMA];
+    const float *lam = inst + L.lam;
+    const float *Mp = Sp + (long long)n * n4, *Vp = Sp + 2LL * n * n4;
+    const float *Up = Sp + 3LL * n * n4, *Utp = Sp + 4LL * n * n4;
+    const bool ball = prm.ctrl_kind == HOPF_BALL;
+    extern __shared__ float4 tsm4[];
+    float *pb = reinterpret_cast<float *>(tsm4);       // [n4] each
+    float *pp = pb + n4, *x0 = pp + n4, *vb = x0 + n4, *ub = vb + n4;
+    float *ys = ub + n4;                                // [G]
+    __shared__ double red[TILE_WARPS];
+    __shared__ float fred[3][TILE_WARPS];
+    __shared__ int s_e;
+    auto fsum3 = [&](float a, float b, float c, float &A, float &B, float &C) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) {
+            fred[0][tid >> 5] = a;
+            fred[1][tid >> 5] = b;
+            fred[2][tid >> 5] = c;
+        }
+        __syncthreads();
+        A = B = C = 0.f;
+        for (int w = 0; w < TILE_WARPS; ++w) {
+            A += fred[0][w];
+            B += fred[1][w];
+            C += fred[2][w];
+        }
+    };
+    const int total = *prm.out_count;
+    for (;;) {
+        if (tid == 0) s_e = atomicAdd(queue2, 1);
+        __syncthreads();
+        const int e = s_e;
+        __syncthreads();
+        if (e >= total) break;
+        const int k = prm.out_list[2 * e], loc = prm.out_list[2 * e + 1];
+        const float *Yp = slot_y + (long long)(loc / PT) * G * PT + (loc % PT);
+        const float *st = prm.out_st + (long long)e * CW;
+        for (int j = tid; j < n4; j += nt) {
+            pb[j] = st[j];
+            pp[j] = st[n4 + j];
+            x0[j] = j < n ? x[(long long)k * n + j] : 0.f;
+        }
+        for (int r = tid; r < G; r += nt) ys[r] = Yp[(long long)r * PT];
+        float tau = st[2 * n4], sigma = st[2 * n4 + 1], tol = st[2 * n4 + 3];
+        int cnt = (int)st[2 * n4 + 2];
+        __syncthreads();
+        for (;;) {
+            ++cnt;
+            const bool check = (cnt % prm.gap_every) == 0 || cnt > prm.max_iter;
+            // dual step, threads over nodes
+            float hp = 0.f;
+            for (int i = tid; i < N; i += nt) {
+                const float wi = __ldg(wv + i);
+                float z[16];
+                float nz = 0.f;
+                for (int c = 0; c < m; ++c) {
+                    const float4 *Kr = reinterpret_cast<const float4 *>(Kp + ((long long)i * MPd + c) * n4);
+                    const float4 *P4 = reinterpret_cast<const float4 *>(pb);
+                    float a = 0.f;
+                    for (int q = 0; q < nq; ++q) a = dot4(__ldg(Kr + q), P4[q], a);
+                    z[c] = a;
+                    nz += ball ? a * a : fabsf(a);
+                }
+                if (check) hp = fmaf(wi, ball ? sqrtf(nz) : nz, hp);
+                float nu = 0.f;
+                for (int c = 0; c < m; ++c) {
+                    const float v = fmaf(sigma, z[c], ys[i * MPd + c]);
+                    z[c] = v;
+                    nu = fmaf(v, v, nu);
+                }
+                const float scl = (ball && nu > wi * wi) ? wi * rsqrtf(nu) : 1.f;
+                for (int c = 0; c < m; ++c) ys[i * MPd + c] = ball ? z[c] * scl : fminf(fmaxf(z[c], -wi), wi);
+            }
+            __syncthreads();
+            // K^T y, threads over state components
+            for (int j = tid; j < n4; j += nt) {
+                float r = 0.f;
+                for (int row = 0; row < G; ++row) r = fmaf(__ldg(Kp + (long long)row * n4 + j), ys[row], r);
+                vb[j] = fmaf(tau, x0[j] - r, pp[j]);
+                ub[j] = x0[j] - r;
+            }
+            __syncthreads();
+            bool done = false;
+            if (check) {
+                float qp = 0.f, dp = 0.f;
+                for (int a = tid; a < n; a += nt) {
+                    float mq = 0.f, vq = 0.f;
+                    for (int b = 0; b < n; ++b) {
+                        mq = fmaf(__ldg(Mp + (long long)b * n4 + a), pb[b], mq);
+                        vq = fmaf(__ldg(Vp + (long long)b * n4 + a), ub[b], vq);
+                    }
+                    qp = fmaf(pb[a], fmaf(0.25f, mq, -x0[a]), qp);
+                    dp = fmaf(ub[a], vq, dp);
+                }
+                float H, Q, Dd;
+                fsum3(hp, qp, dp, H, Q, Dd);
+                const float quad = Q + 1.f, Pv = quad + H, Dv = 1.f - Dd;
+                const float gp = rel_gap(Pv, Dv);
+                const float scl = fmaxf(1.f, fmaxf(fabsf(Pv), fabsf(Dv)));
+                int stt = -1;
+                if (!isfinite(Pv) || !isfinite(Dv)) stt = HOPF_NONFINITE;
+                else if (gp + gap_allowance(quad, H, Dv, scl) <= tol) stt = HOPF_OK;
+                else if (cnt > prm.max_iter) stt = HOPF_MAXITER;
+                if (stt == HOPF_OK) {
+                    // float64 re-certification
+                    const double *K64 = inst64 + L.K, *M64 = inst64 + L.M, *V64 = inst64 + L.V;
+                    const double *w64 = inst64 + L.w;
+                    double h64 = 0.0;
+                    for (int i = tid; i < N; i += nt) {
+                        double nz = 0.0;
+                        for (int c = 0; c < m; ++c) {
+                            const double *Kr = K64 + ((long long)i * m + c) * n;
+                            double z = 0.0;
+                            for (int j = 0; j < n; ++j) z = fma(Kr[j], (double)pb[j], z);
+                            nz += ball ? z * z : fabs(z);
+                        }
+                        h64 = fma(w64[i], ball ? sqrt(nz) : nz, h64);
+                    }
+                    const double H64 = block_sum(h64, red);
+                    double q64 = 0.0, d64 = 0.0;
+                    // u = x0 - K^T (shrunk y) in float64, one component per thread, kept
+                    // after the dual rows in shared memory
+                    for (int j = tid; j < n; j += nt) {
+                        double r = 0.0;
+                        for (int i = 0; i < N; ++i)
+                            for (int c = 0; c < m; ++c)
+                                r = fma(K64[((long long)i * m + c) * n + j], (double)ys[i * MPd + c], r);
+                        reinterpret_cast<double *>(ys + G)[j] = (double)x0[j] - (1.0 - 4e-7) * r;
+                    }
+                    __syncthreads();
+                    const double *u64s = reinterpret_cast<const double *>(ys + G);
+                    for (int a = tid; a < n; a += nt) {
+                        double mq = 0.0, vq = 0.0;
+                        for (int b = 0; b < n; ++b) {
+                            mq = fma(M64[(long long)a * n + b], (double)pb[b], mq);
+                            vq = fma(V64[(long long)a * n + b], u64s[b], vq);
+                        }
+                        q64 = fma((double)pb[a], 0.25 * mq - (double)x0[a], q64);
+                        d64 = fma(u64s[a], vq, d64);
+                    }
+                    const double quad64 = block_sum(q64, red) + 1.0;
+                    const double D64 = 1.0 - block_sum(d64, red);
+                    const double P64 = quad64 + H64;
+                    const double g64 = rel_gap(P64, D64);
+                    const double s64 = fmax(1.0, fmax(fabs(P64), fabs(D64)));
+                    if (g64 + gap_allowance(quad64, H64, D64, s64) <= prm.tol_gap) {
+                        if (tid == 0) {
+                            phi[k] = (float)(-P64);
+                            gap_out[k] = (float)g64;
+                            iters[k] = cnt - 1;
+                            status[k] = HOPF_OK;
+                        }
+                        done = true;
+                    } else {
+                        tol *= 0.5f;
+                        if (cnt > prm.max_iter) stt = HOPF_MAXITER;
+                    }
+                    __syncthreads();
+                }
+                if (!done && stt >= 0 && stt != HOPF_OK) {
+                    if (tid == 0) {
+                        phi[k] = -Pv;
+                        gap_out[k] = gp;
+                        iters[k] = cnt - 1;
+                        status[k] = stt;
+                    }
+                    done = true;
+                }
+            }
+            if (done) {
+                for (int a = tid; a < n; a += nt) pstar[(long long)k * n + a] = pb[a];
+                __syncthreads();
+                break;
+            }
+            // prox of Eq. 37 (plain) or through the eigenvectors of M (accelerated)
+            float pn = 0.f;
+            const int a = tid;
+            if (!prm.accel) {
+                if (a < n4)
+                    for (int b = 0; b < n; ++b) pn = fmaf(__ldg(Sp + (long long)b * n4 + a), vb[b], pn);
+            } else {
+                float w = 0.f;
+                if (a < n4)
+                    for (int b = 0; b < n; ++b) w = fmaf(__ldg(Up + (long long)b * n4 + a), vb[b], w);
+                __syncthreads();
+                if (a < n4) ub[a] = a < n ? w / fmaf(0.5f * tau, __ldg(lam + a), 1.f) : 0.f;
+                __syncthreads();
+                if (a < n4)
+                    for (int b = 0; b < n; ++b) pn = fmaf(__ldg(Utp + (long long)b * n4 + a), ub[b], pn);
+            }
+            const float th = prm.accel ? rsqrtf(fmaf(2.f * gamma, tau, 1.f)) : 1.f;
+            __syncthreads();
+            if (a < n4) {
+                pb[a] = fmaf(th, pn - pp[a], pn);
+                pp[a] = pn;
+            }
+            if (prm.accel) {
+                tau *= th;
+                sigma /= th;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -711,11 +988,34 @@ static cudaError_t launch_tile_t(const float *inst, const double *inst64, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x, const float *p_init,
-                             float *phi, float *pstar, float *gap, int *iters, int *status, float *ws, int *queue,
-                             int ppt, int grid, size_t smem, int dbuf, cudaStream_t s) {
-    const int n = prm.n, m = prm.m, N = prm.N;
+// the tail kernel's dynamic shared memory: pbar, p, x0, v, u [n4], the dual
+// rows [chunks cr] and the float64 u of the re-certification [n]
+size_t tile_tail_smem(int n, int m, int N, int ppt) {
     const TileGeom g = tile_geom(n, m, N, ppt);
+    return sizeof(float) * ((size_t)7 * g.n4 + (size_t)g.chunks * g.cr);
+}
+
+// parked-point state: pbar, p [n4] and tau, sigma, count, tolerance
+long long tile_carry_floats(int n, int m, int N, int ppt, int P) {
+    const TileGeom g = tile_geom(n, m, N, ppt);
+    return (long long)P * (2 * g.n4 + 4);
+}
+
+// queue: 3 device ints (the tiled kernel's queue, the tail's queue, the
+// parked count).  carry_st / carry_list (tile_carry_floats, 2 P ints) enable
+// parking and the tail kernel; null runs the tiled kernel alone.
+cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm_in, const float *x,
+                             const float *p_init, float *phi, float *pstar, float *gap, int *iters, int *status,
+                             float *ws, int *queue, int ppt, int grid, size_t smem, int dbuf, float *carry_st,
+                             int *carry_list, cudaStream_t s) {
+    const int n = prm_in.n, m = prm_in.m, N = prm_in.N;
+    const TileGeom g = tile_geom(n, m, N, ppt);
+    const size_t tsmem = tile_tail_smem(n, m, N, ppt);
+    SolveParams prm = prm_in;
+    prm.carry_cap = (carry_st && carry_list && tsmem <= 200 * 1024) ? 1 : 0;
+    prm.out_st = carry_st;
+    prm.out_list = carry_list;
+    prm.out_count = queue + 2;
     float *Kp = ws;
     float *Sp = Kp + (long long)g.chunks * g.cr * g.n4;
     float *Mp = Sp + (long long)n * g.n4;
@@ -723,17 +1023,18 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
     float *sp = Vp + 3LL * n * g.n4;             // after V come U and U^T
     float *sx = sp + (long long)grid * g.n4 * g.pt;
     float *sy = sx + (long long)grid * g.n4 * g.pt;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(queue, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     tile_pad_kernel<<<256, 256, 0, s>>>(inst, n, m, N, g, Kp, Sp, Mp, Vp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 #define TILE_CASE(MPV)                                                                                        \
     case MPV:                                                                                                 \
-        return ppt == 2 ? launch_tile_t<MPV, 2>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                                status, sp, sx, sy, queue, grid, smem, dbuf, s)                    \
-                        : launch_tile_t<MPV, 1>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                                status, sp, sx, sy, queue, grid, smem, dbuf, s);
+        e = ppt == 2 ? launch_tile_t<MPV, 2>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
+                                             status, sp, sx, sy, queue, grid, smem, dbuf, s)                    \
+                     : launch_tile_t<MPV, 1>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
+                                             status, sp, sx, sy, queue, grid, smem, dbuf, s);                   \
+        break;
     switch (g.mp) {
         TILE_CASE(1)
         TILE_CASE(2)
@@ -749,6 +1050,14 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
             return cudaErrorInvalidValue;
     }
 #undef TILE_CASE
+    if (e != cudaSuccess || !prm.carry_cap) return e;
+    if (tsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(pdhg_tile_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+        if (e != cudaSuccess) return e;
+    }
+    pdhg_tile_tail_kernel<<<4 * grid, 256, tsmem, s>>>(inst, inst64, Kp, Sp, prm, ppt, x, phi, pstar, gap, iters,
+                                                        status, sy, queue + 1);
+    return cudaGetLastError();
 }
 
 }  // namespace hopf
