@@ -395,10 +395,11 @@ def run_secondary(args):
         "cpu_baseline": cpu,
         "e2e": {"value": shard.job_throughput(ok_e2e, world, t_local[1] * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": points * n * 4, "d2h_bytes_per_step": points * 8},
-        # horizons, tables, (pad | expand), solve; the warm start adds the network
+        # chain: horizons, tables, pad, tiled solve, tail; dimension: horizons,
+        # expand, tables, stacked solve.  The warm start adds the network
         # (standardise + 3 tensor-core GEMMs), 3 ordering kernels, the fallback
-        # list and a second pad + solve
-        "gpu_launches": (14 if warm_info else 4) * args.steps,
+        # list and a second pad + solve + tail
+        "gpu_launches": (16 if warm_info else (5 if args.workload == "chain" else 4)) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -476,7 +477,9 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
                      "timing": "whole step (tables + solves; systems overlap on the side streams)"},
         "cpu_baseline": cpu,
         "e2e": None,
-        "gpu_launches": 4 * len(systems) * args.steps,
+        # per system: horizons, tables and either pad + tiled solve + tail or
+        # the three small-state phases
+        "gpu_launches": 5 * len(systems) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
