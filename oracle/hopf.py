@@ -16,6 +16,9 @@ Control and Trajectory Generation in High-Dimensional Systems"):
   * primal-dual iteration ................... §III, Eq. 15 with Eq. 22, Eq. 23, Eq. 37
   * accelerated iteration for a strongly convex G (named in §III, from
     Chambolle and Pock 2011, Algorithm 2) ..... pdhg(..., accel=True)
+  * the same minimisation in terminal-time variables p = e^{T A^T} q
+    (an exact substitution in Eq. 18; a preconditioning of Eq. 15) ......
+                                              setup(..., variables="terminal")
   * duality gap (stopping rule) ............. §III.B (primal/dual residuals) and
                                               the Fenchel dual of Eq. 18
   * time-to-reach ........................... §IV (zero of phi(x, T) in T, bisection)
@@ -126,6 +129,19 @@ def node_matrices(sysd, T, N, rule):
     return K
 
 
+def node_matrices_terminal(sysd, T, N, rule):
+    """Node matrices of Eq. 18 after the substitution p = e^{T A^T} q:
+    K_i e^{T A^T} = (-e^{-(T - t_i) A} B Q)^T e^{T A^T} = (-e^{t_i A} B Q)^T,
+    shape (N, m, n), one direct expm per node (forward times t_i of Eq. 17)."""
+    A, B = sysd["A"], sysd["B"]
+    Q = control_scaling(sysd)
+    t, _ = nodes(T, N, rule)
+    K = np.empty((N, B.shape[1], A.shape[0]))
+    for i in range(N):
+        K[i] = -(expm(t[i] * A) @ B @ Q).T
+    return K
+
+
 def terminal_matrices(sysd, T):
     """Quadratic target cost of §VI.A.  J_x(x) = x^T W^-1 x - 1 (Eq. 34), so
     J_z(z) = z^T V z - 1 with V = e^{T A^T} W^-1 e^{T A}, and its conjugate is
@@ -139,22 +155,42 @@ def terminal_matrices(sysd, T):
     return M, 0.5 * (V + V.T)
 
 
-def setup(sysd, T, N, rule, tau, sigma_scale=1.0):
+def setup(sysd, T, N, rule, tau, sigma_scale=1.0, variables="initial"):
     """All data of one primal-dual problem at horizon T.
 
     K (N, m, n) from Eq. 20, weights w (N,), M and V (Eq. 35), the prox matrix
     S = (I + tau M / 2)^-1 of Eq. 37, L2 = |K|_2^2 (largest eigenvalue of
-    K^T K) and the dual step sigma = 1 / (tau |K|^2) of §VI (times sigma_scale)."""
-    K = node_matrices(sysd, T, N, rule)
+    K^T K) and the dual step sigma = 1 / (tau |K|^2) of §VI (times sigma_scale).
+
+    variables="terminal" sets the same problem up in the variable q of
+    p = E^T q, E = e^{TA} (the costate carried to the terminal time).  Every
+    term of Eq. 18 keeps its form: K_i p = K'_i q with K'_i = (-e^{t_i A} B Q)^T,
+    p^T M p = q^T W q (M' = W, V' = W^-1), <z0, p> = <E z0, q>.  The objective
+    values P and D and the gap are unchanged; the primal-dual iteration of
+    Eq. 15 run in q is a different (preconditioned) iteration with the same
+    solution p* = E^T q*.  E is returned (identity for variables="initial"),
+    and value() maps x and p in and out."""
+    n = sysd["A"].shape[0]
     _, w = nodes(T, N, rule)
-    M, V = terminal_matrices(sysd, T)
-    n = M.shape[0]
+    if variables == "initial":
+        K = node_matrices(sysd, T, N, rule)
+        M, V = terminal_matrices(sysd, T)
+        E = np.eye(n)
+    elif variables == "terminal":
+        K = node_matrices_terminal(sysd, T, N, rule)
+        W = sysd["W"]
+        M = 0.5 * (W + W.T)
+        V = np.linalg.inv(M)
+        V = 0.5 * (V + V.T)
+        E = expm(T * sysd["A"])
+    else:
+        raise ValueError("variables must be 'initial' or 'terminal'")
     Kf = K.reshape(-1, n)
     L2 = float(np.linalg.eigvalsh(Kf.T @ Kf)[-1])
     S = np.linalg.inv(np.eye(n) + 0.5 * tau * M)
     return dict(K=K, w=w, M=M, V=V, S=S, L2=L2, tau=float(tau),
                 sigma=float(sigma_scale) / (float(tau) * L2),
-                kind=sysd["ctrl_kind"], T=float(T))
+                kind=sysd["ctrl_kind"], T=float(T), E=E, variables=variables)
 
 
 def _batched(prob_list):
@@ -301,10 +337,32 @@ def terminal_cost(sysd, x):
     return np.einsum("...i,ij,...j->...", x, Wi, x) - 1.0
 
 
-def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_scale=1.0, accel=False):
+def solve_in_variables(probs, x, p0=None, **kw):
+    """pdhg() for per-point problems probs (a list, one per row of x, or one
+    shared problem) in the problems' variables: rows of x and of the warm
+    start p0 are mapped to q (x' = E x, q0 = E^-T p0), and the solution back
+    to p = E^T q.  The returned dict carries p (original variables) and q."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    shared = isinstance(probs, dict)
+    Es = np.broadcast_to(probs["E"], (x.shape[0],) + probs["E"].shape) if shared else \
+        np.stack([pr["E"] for pr in probs])
+    xq = np.einsum("kij,kj->ki", Es, x)
+    q0 = None if p0 is None else np.linalg.solve(np.transpose(Es, (0, 2, 1)),
+                                                 np.atleast_2d(np.asarray(p0, dtype=np.float64))[..., None])[..., 0]
+    r = pdhg(probs if shared else _batched(probs), xq, p0=q0, **kw)
+    r["q"] = r["p"]
+    r["p"] = np.einsum("kji,kj->ki", Es, r["q"])
+    return r
+
+
+def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_scale=1.0, accel=False,
+          variables="initial"):
     """phi_N(x, T): the generalized Hopf formula with the N-node quadrature
     (Eq. 18) for every row of x at one horizon T.  At T = 0 the value is the
-    terminal cost itself (Eq. 4 initial condition) and p* = grad J_x."""
+    terminal cost itself (Eq. 4 initial condition) and p* = grad J_x.
+    variables="terminal" runs the iteration in the variable q (see setup);
+    phi, P, D and the gap are the same quantities, p is returned in the
+    original variable."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     if T == 0.0:
         Wi = np.linalg.inv(sysd["W"])
@@ -312,8 +370,10 @@ def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_sc
         return dict(phi=terminal_cost(sysd, x), p=2.0 * x @ Wi.T, gap=np.zeros(P_),
                     iters=np.zeros(P_, dtype=np.int64), status=np.zeros(P_, dtype=np.int64),
                     P=-terminal_cost(sysd, x), D=-terminal_cost(sysd, x))
-    prob = setup(sysd, T, N, rule, tau, sigma_scale)
-    return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0, accel=accel)
+    prob = setup(sysd, T, N, rule, tau, sigma_scale, variables)
+    if variables == "initial":
+        return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0, accel=accel)
+    return solve_in_variables(prob, x, p0=p0, tol=tol, max_iter=max_iter, accel=accel)
 
 
 # ---------------------------------------------------------------- time-to-reach
@@ -325,7 +385,7 @@ def hamiltonian_x(sysd, p, x0):
 
 
 def time_to_reach(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-8,
-                  sign_floor=1e-13, max_iter=400000, sigma_scale=1.0):
+                  sign_floor=1e-13, max_iter=400000, sigma_scale=1.0, variables="initial"):
     """Minimum time T* to reach the target (§IV): the smallest T with
     phi_N(x, T) <= 0, found by bisection on [0, t_max].
 
@@ -336,6 +396,7 @@ def time_to_reach(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-8,
     shrinks until hi - lo <= tol_T * hi; T* = hi, and p* is the solution at hi
     solved to tol_gap.  Points already inside the target return T* = 0;
     points with phi(t_max) > 0 return UNREACHABLE.  Every point is independent.
+    Every inner solve runs in the given variables (see setup).
     Returns dict(T, p, status, steps)."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     P_, n = x.shape
@@ -346,10 +407,9 @@ def time_to_reach(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-8,
 
     def sign_solve(idx, Tvals):
         """phi <= 0 ? for the points idx at their own horizons Tvals."""
-        probs = [setup(sysd, float(Tv), N, rule, tau, sigma_scale) for Tv in Tvals]
-        bp = _batched(probs)
-        r = pdhg(bp, x[idx], tol=sign_floor, max_iter=max_iter,
-                 stop=lambda Pa, Da: (Pa < 0.0) | (Da > 0.0))
+        probs = [setup(sysd, float(Tv), N, rule, tau, sigma_scale, variables) for Tv in Tvals]
+        r = solve_in_variables(probs, x[idx], tol=sign_floor, max_iter=max_iter,
+                               stop=lambda Pa, Da: (Pa < 0.0) | (Da > 0.0))
         # phi = -P(p*) lies in [-P, -D]
         reached = r["D"] > 0.0
         amb = ~(reached | (r["P"] < 0.0))
@@ -379,15 +439,15 @@ def time_to_reach(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-8,
         todo = todo[hi[todo] - lo[todo] > tol_T * hi[todo]]
     fin = np.where(~inside & (st != UNREACHABLE))[0]
     if fin.size:
-        probs = [setup(sysd, float(hi[i]), N, rule, tau, sigma_scale) for i in fin]
-        r = pdhg(_batched(probs), x[fin], tol=tol_gap, max_iter=max_iter)
+        probs = [setup(sysd, float(hi[i]), N, rule, tau, sigma_scale, variables) for i in fin]
+        r = solve_in_variables(probs, x[fin], tol=tol_gap, max_iter=max_iter)
         T_out[fin] = hi[fin]
         p_out[fin] = r["p"]
     return dict(T=T_out, p=p_out, status=st, steps=steps)
 
 
 def time_to_reach_newton(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-10, max_steps=100,
-                         max_iter=400000, sigma_scale=1.0):
+                         max_iter=400000, sigma_scale=1.0, variables="initial"):
     """Minimum time to reach by the hybrid of §IV: Newton steps on phi(x, T)
     using the HJ equation for the derivative, t_{k+1} = t_k + phi / H_x(p*, x0)
     (Eq. 26 with H_x of §IV), safeguarded by the bracket [lo, hi] that the
@@ -404,8 +464,8 @@ def time_to_reach_newton(sysd, x, t_max, N, rule, tau, tol_T=1e-6, tol_gap=1e-10
     st = np.zeros(P_, dtype=np.int64)
 
     def solve(idx, Tvals):
-        probs = [setup(sysd, float(Tv), N, rule, tau, sigma_scale) for Tv in Tvals]
-        return pdhg(_batched(probs), x[idx], tol=tol_gap, max_iter=max_iter)
+        probs = [setup(sysd, float(Tv), N, rule, tau, sigma_scale, variables) for Tv in Tvals]
+        return solve_in_variables(probs, x[idx], tol=tol_gap, max_iter=max_iter)
 
     inside = terminal_cost(sysd, x) <= 0.0
     p_out[inside] = 2.0 * x[inside] @ Wi.T

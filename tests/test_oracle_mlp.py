@@ -50,3 +50,27 @@ def test_adam_first_step_is_signed_lr():
     v = [np.zeros(3)]
     om.adam_step(p, g, m, v, 1, 0.01)
     assert np.allclose(p[0], [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01 * 1e-3 / (1e-3 + 1e-8)], atol=1e-12)
+
+
+def test_adam_constant_gradient_steps_and_second_step_closed_form():
+    # With a constant gradient the bias-corrected moments are exactly g and g^2
+    # at every step, so each step is -lr g / (|g| + eps); a wrong bias-correction
+    # exponent shows from the second step on.
+    g0 = np.array([0.5, -4.0, 2e-3])
+    p = [np.array([1.0, -2.0, 3.0])]
+    m, v = [np.zeros(3)], [np.zeros(3)]
+    want = p[0].copy()
+    for step in range(1, 6):
+        om.adam_step(p, [g0.copy()], m, v, step, 0.01)
+        want = want - 0.01 * g0 / (np.abs(g0) + 1e-8)
+        assert np.allclose(p[0], want, rtol=0, atol=1e-12), step
+    # two different gradients: m_hat = (b1 g1 + g2)/(1 + b1), v_hat = (b2 g1^2 + g2^2)/(1 + b2)
+    g1, g2 = np.array([1.0, -0.3]), np.array([-2.0, 0.7])
+    p = [np.zeros(2)]
+    m, v = [np.zeros(2)], [np.zeros(2)]
+    om.adam_step(p, [g1], m, v, 1, 0.1, beta1=0.8, beta2=0.9, eps=0.0)
+    after1 = p[0].copy()
+    om.adam_step(p, [g2], m, v, 2, 0.1, beta1=0.8, beta2=0.9, eps=0.0)
+    mh = (0.8 * g1 + g2) / 1.8
+    vh = (0.9 * g1 ** 2 + g2 ** 2) / 1.9
+    assert np.allclose(p[0] - after1, -0.1 * mh / np.sqrt(vh), rtol=1e-13)

@@ -61,6 +61,18 @@ def test_di_node_matrices_closed_form():
         assert np.allclose(K[:, 0, 1], -1.0, atol=1e-14)
 
 
+def test_di_terminal_variable_node_matrices_closed_form():
+    # After p = e^{T A^T} q the node matrices are (-e^{t_i A} B)^T; for the
+    # double integrator e^{tA} B = [t, 1]^T, so K'_i = [-t_i, -1], and M' = W.
+    sysd = wl.double_integrator(0.2)
+    for rule in (oh.LEFT_RIEMANN, oh.TRAPEZOID):
+        prob = oh.setup(sysd, 1.7, 9, rule, 1.0, variables="terminal")
+        t, _ = oh.nodes(1.7, 9, rule)
+        assert np.allclose(prob["K"][:, 0, 0], -t, atol=1e-14)
+        assert np.allclose(prob["K"][:, 0, 1], -1.0, atol=1e-14)
+        assert np.allclose(prob["M"], 0.04 * np.eye(2)) and np.allclose(prob["E"], [[1.0, 1.7], [0.0, 1.0]])
+
+
 def test_terminal_matrices_closed_form_di():
     # M = e^{-TA} W e^{-TA}^T with e^{-TA} = [[1, -T], [0, 1]].
     sysd = wl.double_integrator(0.3)
@@ -117,55 +129,62 @@ def test_single_integrator_time_to_reach_closed_form():
 
 
 # ---------------------------------------------- strong duality, other solvers
-def test_value_equals_independent_projected_gradient_box_di():
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_value_equals_independent_projected_gradient_box_di(variables):
     # phi_N from the PDHG (dual form) equals the discrete-control minimum
-    # computed by an unrelated algorithm (FISTA on the primal control form).
+    # computed by an unrelated algorithm (FISTA on the primal control form),
+    # in the paper's variable p and in the terminal-time variable q.
     sysd = wl.double_integrator(0.1)
     for T, x0 in [(1.0, np.array([0.6, -0.3])), (2.0, np.array([-1.2, 0.9]))]:
-        res = oh.value(sysd, x0, T, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12)
+        res = oh.value(sysd, x0, T, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, variables=variables)
         ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, T, 32, "box", trapezoid=True)
         assert abs(res["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
 
 
-def test_value_equals_independent_projected_gradient_ball_random():
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_value_equals_independent_projected_gradient_ball_random(variables):
     sysd = wl.random_system(11, 4, 2)
     x = wl.normal_points(12, 3, 4, 1.0)
-    res = oh.value(sysd, x, 0.8, 24, oh.LEFT_RIEMANN, tau=0.2, tol=1e-12)
+    res = oh.value(sysd, x, 0.8, 24, oh.LEFT_RIEMANN, tau=0.2, tol=1e-12, variables=variables)
     for k in range(3):
         ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x[k], 0.8, 24, "ball")
         assert abs(res["phi"][k] - ref) <= 1e-8 * max(1.0, abs(ref)), (k, res["phi"][k], ref)
 
 
-def test_value_equals_brute_force_enumeration():
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_value_equals_brute_force_enumeration(variables):
     # Exhaustive active-set enumeration is exact on N <= 8 scalar-control nodes.
     sysd = wl.double_integrator(0.2)
     for T, x0, rule in [(1.3, np.array([0.5, 0.4]), oh.LEFT_RIEMANN),
                         (0.7, np.array([-0.3, 0.8]), oh.TRAPEZOID)]:
-        res = oh.value(sysd, x0, T, 6, rule, tau=2.0, tol=1e-13)
+        res = oh.value(sysd, x0, T, 6, rule, tau=2.0, tol=1e-13, variables=variables)
         ref = ind.brute_force_value(sysd["A"], sysd["B"], sysd["W"], x0, T, 6,
                                     trapezoid=(rule == oh.TRAPEZOID))
         assert abs(res["phi"][0] - ref) <= 1e-9 * max(1.0, abs(ref)), (res["phi"][0], ref)
 
 
-def test_duality_gap_certifies_interval():
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_duality_gap_certifies_interval(variables):
     # Weak duality: D(y) <= phi <= ... i.e. -P <= phi <= -D for any feasible pair,
     # and the independent optimum lies inside [-P, -D] at every tolerance.
     sysd = wl.double_integrator(0.1)
     x0 = np.array([0.9, 0.2])
     ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 16, "box", trapezoid=True)
     for tol in (1e-2, 1e-4, 1e-6):
-        r = oh.value(sysd, x0, 1.0, 16, oh.TRAPEZOID, tau=2.0, tol=tol)
+        r = oh.value(sysd, x0, 1.0, 16, oh.TRAPEZOID, tau=2.0, tol=tol, variables=variables)
         assert -r["P"][0] - 1e-12 <= ref <= -r["D"][0] + 1e-12
         assert r["gap"][0] <= tol
 
 
 # ----------------------------------------------------------- calculus pins
-def test_gradient_identity_finite_differences():
-    # Eq. 24: p* = grad_z phi (= grad_x phi at t = 0).
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_gradient_identity_finite_differences(variables):
+    # Eq. 24: p* = grad_z phi (= grad_x phi at t = 0).  In terminal-time
+    # variables this also pins the map back p = e^{T A^T} q.
     sysd = wl.random_system(5, 3, 1)
     x0 = np.array([0.8, -0.5, 0.3])
     T, N = 0.6, 20
-    base = oh.value(sysd, x0, T, N, oh.LEFT_RIEMANN, tau=0.3, tol=1e-13)
+    base = oh.value(sysd, x0, T, N, oh.LEFT_RIEMANN, tau=0.3, tol=1e-13, variables=variables)
     h = 1e-4
     fd = np.zeros(3)
     for j in range(3):
@@ -287,6 +306,21 @@ def test_accelerated_iteration_reaches_the_same_value():
     r1 = oh.value(sysd, x0, 1.0, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, accel=True)
     ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 32, "box", trapezoid=True)
     assert abs(r1["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
+
+
+def test_terminal_variables_time_to_reach_matches_switching_curve_bound():
+    # The bisection in terminal-time variables finds the same T* as in the
+    # paper's variables, inside the switching-curve bound of the double integrator.
+    sysd = wl.double_integrator(0.1)
+    x = np.array([[1.0, 0.5], [-1.2, 0.3]])
+    rt = oh.time_to_reach(sysd, x, 8.0, 64, oh.TRAPEZOID, tau=2.0, tol_T=1e-8, variables="terminal")
+    ri = oh.time_to_reach(sysd, x, 8.0, 64, oh.TRAPEZOID, tau=2.0, tol_T=1e-8)
+    assert np.allclose(rt["T"], ri["T"], rtol=1e-7), (rt["T"], ri["T"])
+    for k in range(2):
+        T0 = ind.di_min_time_to_origin(x[k])
+        assert 0.0 <= T0 - rt["T"][k] <= 0.1 + 2.0 * np.sqrt(0.1 + 0.005) + 1e-2
+    # p* at gap 1e-8 is fixed only to about sqrt(gap / lambda_min(M)) here
+    assert np.allclose(rt["p"], ri["p"], rtol=1e-3, atol=1e-6)
 
 
 def test_newton_time_to_reach_matches_closed_form_and_bisection():
