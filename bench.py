@@ -40,6 +40,8 @@ METRIC = "Hopf solves/sec at gap<=1e-5: warm-start batched vs plain cold PDHG, s
 POINTS = 65536
 TOL = 1e-5
 TAU_ACCEL = 2.0
+TAU_TERM = 0.5       # Eq. 15 in terminal-time variables (oracle sweep: mean 80 iterations vs 110 at 0.3)
+PARK_TERM = 256
 TRAIN_POINTS = 262144
 TRAIN_EPOCHS = 60
 
@@ -128,20 +130,66 @@ print(json.dumps(dict(dt=dt, ok=int((r["status"] == 0).sum()), iters=float(r["it
     return d["ok"] / d["dt"], d
 
 
+def _oracle_slice(job):
+    """Worker of the all-core oracle timing: solves points [lo, hi) of the
+    headline workload with the FP64 oracle (one thread) and reports the time."""
+    lo, hi = job
+    from oracle import hopf as oh
+    w = wl.workload_random10(hi)
+    t0 = time.perf_counter()
+    r = oh.value(w["system"], w["x"][lo:hi], w["t"], w["N"], w["rule"], tau=w["tau"], tol=TOL, max_iter=100000)
+    return time.perf_counter() - t0, int((r["status"] == 0).sum()), float(r["iters"].sum())
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core (spawned before any
+    CUDA work); a step hands each process its own slice of the points."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                                "CUDA_VISIBLE_DEVICES")}
+        os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        self.pool.map(_oracle_slice, [(0, 1)] * self.procs)          # imports and warm-up
+
+    def step(self, per_proc):
+        """Wall time and certified solves of procs x per_proc points."""
+        jobs = [(k * per_proc, (k + 1) * per_proc) for k in range(self.procs)]
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_slice, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        return wall, sum(o[1] for o in out), sum(o[2] for o in out) / (self.procs * per_proc)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
         return
-    sample = 96
+    pool = OraclePool()
+    per_proc = 48
+    sample = per_proc * pool.procs
     times, ok_total, t_all = [], 0, 0.0
     for step in range(args.warmup + args.steps):
-        v, d = cpu_oracle_sample(sample)
+        dt, ok, _ = pool.step(per_proc)
         if step >= args.warmup:
-            times.append(d["dt"])
-            ok_total += d["ok"]
-            t_all += d["dt"]
+            times.append(dt)
+            ok_total += ok
+            t_all += dt
+    pool.close()
     value = ok_total / t_all
-    desc = (f"FP64 numpy oracle, 1 thread, first {sample} of the {POINTS} points per step, "
+    desc = (f"FP64 numpy oracle (the paper's iteration, Eq. 15), one process per host core "
+            f"({pool.procs} cores, 1 thread each), {sample} of the {POINTS} points per step, "
             f"gap<=1e-5, same system/t/N/tau")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
@@ -149,21 +197,23 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": "random_n10_m2_t2_N256_65536pts", "n": 10, "m": 2, "N": 256, "t": 2.0,
                        "points": POINTS, "sample_points_per_step": sample, "tol_gap": TOL},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": pool.procs, "kind": "oracle",
+                             "sample": desc},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def train_warm_start(H, sysd, w, rank):
     """Untimed set-up: label 262,144 fresh points with the GPU solver (cold,
-    accelerated, gap 2e-6) and train the warm-start network on them with the
-    library's own forward/backward/Adam kernels."""
+    terminal-time variables, gap 2e-6) and train the warm-start network on
+    them with the library's own forward/backward/Adam kernels."""
     import torch
     from paper_1712_08226_gb300.warmstart import WarmStartNet
     t0 = time.perf_counter()
     xtr = torch.tensor(wl.normal_points(40 + 1000 * rank, TRAIN_POINTS, 10, 2.0), dtype=torch.float32,
                        device="cuda")
-    lab = H.value(sysd, xtr, w["t"], H.Options(N=w["N"], tau=TAU_ACCEL, tol_gap=2e-6, accel=True))
+    lab = H.value(sysd, xtr, w["t"], H.Options(N=w["N"], tau=TAU_TERM, tol_gap=2e-6,
+                                               variables=H.VARS_TERMINAL))
     torch.cuda.synchronize()
     t_label = time.perf_counter() - t0
     net = WarmStartNet(10, 10, hidden=256, seed=0)
@@ -191,7 +241,7 @@ def oracle_sample_seconds(code_body, timeout=900):
 
 SECONDARY = {
     # 100-mass spring chain, value at a shared horizon: the tiled large-state kernel
-    "chain": dict(points=4096, T=10.0, N=512, tau=0.5, cpu_points=1),
+    "chain": dict(points=4096, T=10.0, N=512, tau=0.5, tau_terminal=0.1, cpu_points=1),
     # 60 double-integrator samples sharing one control (d = 120): the structured
     # stacked-copy solve, with the dense stacked system as comparison
     "dimension": dict(points=16384, T=2.5, d=120, cpu_points=2),
@@ -211,13 +261,14 @@ def run_secondary(args):
     if args.workload == "chain":
         sysd = wl.spring_chain()
         x = wl.normal_points(3 + 1000 * rank, points, 200, 1.0)
-        n, m, N, T, tau = 200, 10, cfg["N"], cfg["T"], cfg["tau"]
+        n, m, N, T = 200, 10, cfg["N"], cfg["T"]
+        tau = cfg["tau"] if args.paper_variables else cfg["tau_terminal"]
         fpi = flops_per_point_iter(n, m, N)
         wname = f"spring_chain_n200_m10_box_N512_T10_{points}pts"
         kernel = "pdhg_tile_kernel<10,1>"
         cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
                     f"x = wl.normal_points(3, {cfg['cpu_points']}, 200, 1.0)\nt0 = time.perf_counter()\n"
-                    f"r = oh.value(wl.spring_chain(), x, {T}, {N}, oh.LEFT_RIEMANN, tau={tau}, tol={TOL}, "
+                    f"r = oh.value(wl.spring_chain(), x, {T}, {N}, oh.LEFT_RIEMANN, tau={cfg['tau']}, tol={TOL}, "
                     f"max_iter=200000, accel={bool(args.accel)})\n"
                     f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
     elif args.workload == "ragged":
@@ -275,7 +326,9 @@ def run_secondary(args):
         run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel, N, T, tau)
         return
     x_dev = torch.tensor(x, dtype=torch.float32, device="cuda")
-    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True, accel=accel)
+    variables = H.VARS_TERMINAL if (args.workload == "chain" and not args.paper_variables) else H.VARS_INITIAL
+    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True, accel=accel,
+                     variables=variables)
     warm_info = None
     if args.workload == "chain" and args.warm:
         # untimed set-up: label seeded training points with the GPU solver
@@ -383,6 +436,7 @@ def run_secondary(args):
         "data": "synthetic (seeded)",
         "config": {"workload": wname, "n": n, "m": m, "N": N, "t": T, "points_per_gpu": points, "tol_gap": TOL,
                    "tau": tau, "iteration": "accelerated (strongly convex G)" if accel else "Eq. 15 (theta = 1)",
+                   "variables": "terminal-time q (p = e^{TA^T} q)" if variables else "paper's p",
                    "l2": "flushed between timed steps (512 MB write)",
                    "mean_iters": float(res["iters"].mean()), "max_iters": int(res["iters"].max()),
                    "certified_per_step": res["ok"] / args.steps, "ms_solve": statistics.mean(res["solve_ms"]),
@@ -399,7 +453,8 @@ def run_secondary(args):
         # expand, tables, stacked solve.  The warm start adds the network
         # (standardise + 3 tensor-core GEMMs), 3 ordering kernels, the fallback
         # list and a second pad + solve + tail
-        "gpu_launches": (16 if warm_info else (5 if args.workload == "chain" else 4)) * args.steps,
+        "gpu_launches": (16 if warm_info else (5 if args.workload == "chain" else 4)) * args.steps
+                        + (2 * args.steps if variables else 0),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -599,6 +654,9 @@ def run_trajectory(args):
     print(json.dumps(line), flush=True)
 
 
+w0_tau = wl.workload_random10(1)["tau"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -616,6 +674,8 @@ def main():
                     choices=["random10", "chain", "dimension", "ragged", "trajectory", "chain_ttr"],
                     help="random10: the headline; chain / dimension: secondary workloads")
     ap.add_argument("--accel", action="store_true", help="secondary chain workload: accelerated steps")
+    ap.add_argument("--paper-variables", action="store_true",
+                    help="chain workload: iterate in the paper's variable p instead of terminal-time variables")
     ap.add_argument("--warm", action="store_true", help="secondary chain workload: learned warm start")
     ap.add_argument("--newton", action="store_true", help="chain_ttr workload: Newton hybrid instead of bisection")
     ap.add_argument("--t-max", type=float, default=40.0, help="chain_ttr workload: upper end of the bracket")
@@ -638,14 +698,24 @@ def main():
         return
     rank, world, local = rank_env()
 
-    # CPU baseline first (fresh single-threaded process, before any CUDA work)
+    # CPU baseline first (before any CUDA work): the FP64 oracle on one core
+    # (fresh single-threaded process) and on every host core (one spawned
+    # single-threaded process per core, each on its own slice of the points)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = 1024
-        v, d = cpu_oracle_sample(sample)
-        cpu = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, 1 thread, first {sample} of the {POINTS} points, gap<=1e-5, "
-                         f"{d['dt']:.1f} s, mean {d['iters']:.0f} iterations"}
+        sample = 512
+        v1, d = cpu_oracle_sample(sample)
+        pool = OraclePool()
+        per_proc = 96
+        wall, ok_all, it_all = pool.step(per_proc)
+        pool.close()
+        cpu = {"value": ok_all / wall, "unit": "solves/s", "cores": pool.procs, "kind": "oracle",
+               "sample": f"FP64 numpy oracle (the paper's iteration, Eq. 15, tau {w0_tau}): {pool.procs} processes x "
+                         f"1 thread, {per_proc} points each ({pool.procs * per_proc} of the {POINTS} points), "
+                         f"gap<=1e-5, {wall:.1f} s wall, mean {it_all:.0f} iterations",
+               "single_core": {"value": v1, "unit": "solves/s", "cores": 1,
+                               "ms_per_solve": 1e3 * d["dt"] / max(1, d["ok"]),
+                               "sample": f"first {sample} points, {d['dt']:.1f} s"}}
 
     import torch
     torch.cuda.set_device(local)
@@ -669,22 +739,26 @@ def main():
     x_dev = torch.tensor(w["x"], dtype=torch.float32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
-    # cold start, accelerated steps (strongly convex G), tau0 = 2
-    opts_cold = H.Options(N=N, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
-                          profile=True, accel=True, park_iters=1024)
-    # the paper's iteration (Eq. 15, theta = 1) from the same cold start
+    # the paper's iteration (Eq. 15, theta = 1) from its cold start, in the
+    # paper's variable: the plain cold baseline of the comparison
     opts_plain = H.Options(N=N, tau=w["tau"], tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
                            profile=True, accel=False, park_iters=512)
-    # warm start from the network, accelerated steps, cold fallback
-    opts_warm = H.Options(N=N, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
-                          profile=True, accel=True, park_iters=512)
+    # the accelerated iteration (strongly convex G), paper's variable, cold
+    opts_accel = H.Options(N=N, tau=TAU_ACCEL, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                           profile=True, accel=True, park_iters=1024)
+    # Eq. 15 in terminal-time variables, cold
+    opts_cold = H.Options(N=N, tau=TAU_TERM, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                          profile=True, accel=False, park_iters=PARK_TERM, variables=H.VARS_TERMINAL)
+    # warm start from the network, Eq. 15 in terminal-time variables, cold fallback
+    opts_warm = H.Options(N=N, tau=TAU_TERM, tol_gap=TOL, max_iter=100000, gap_every=8, precision=H.FP32,
+                          profile=True, accel=False, park_iters=PARK_TERM, variables=H.VARS_TERMINAL)
 
     net, train_info = (None, None) if args.cold else train_warm_start(H, sysd, w, rank)
 
     def call(kind):
         if kind == "warm":
             return value_warm(sysd, x_dev, w["t"], net, opts_warm)
-        return H.value(sysd, x_dev, w["t"], opts_cold if kind == "cold" else opts_plain)
+        return H.value(sysd, x_dev, w["t"], {"cold": opts_cold, "plain": opts_plain, "accel": opts_accel}[kind])
 
     def timed(kind, steps):
         """Device time per step (CUDA events on the launching stream), L2 flushed before each."""
@@ -716,7 +790,7 @@ def main():
 
     compare = {}
     if not args.no_compare:
-        for kind in ("plain", "cold") if main_kind == "warm" else ("plain",):
+        for kind in ("plain", "accel", "cold") if main_kind == "warm" else ("plain", "accel"):
             call(kind)
             rr = timed(kind, max(1, min(3, args.steps)))
             compare[kind] = {"solves_per_s": rr["ok"] / len(rr["ms"]) / (statistics.mean(rr["ms"]) * 1e-3),
@@ -778,9 +852,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; random n=10 system, x~N(0,4I))",
         "config": {"workload": f"random_n10_m2_t2_N256_{points}pts", "n": n, "m": m, "N": N, "t": w["t"],
-                   "points_per_gpu": points, "tol_gap": TOL, "tau0": TAU_ACCEL,
+                   "points_per_gpu": points, "tol_gap": TOL, "tau": TAU_TERM,
                    "start": "warm (network prediction), cold fallback" if main_kind == "warm" else "cold",
-                   "iteration": "accelerated (strongly convex G), two-phase",
+                   "iteration": "Eq. 15 in terminal-time variables p = e^{TA^T} q, three phases",
                    "l2": "flushed between timed steps (512 MB write)",
                    "mean_iters": float(iters_last.mean()), "p99_iters": float(np.percentile(iters_last, 99)),
                    "max_iters": int(iters_last.max()), "fallback_points": res["fallback"],

@@ -129,14 +129,34 @@ typedef struct {
                            size; HOPF_KERNEL_GENERIC (1) forces one warp per
                            point (the reference layout of the iteration; used
                            to compare the specialised kernels with it).          */
+    int variables;      /* variable the iteration of Eq. 15 runs in.
+                           HOPF_VARS_INITIAL (0): the paper's p of Eq. 18.
+                           HOPF_VARS_TERMINAL (1): q with p = e^{T A^T} q (the
+                           costate carried to the terminal time).  The
+                           minimisation is the same (Eq. 18 with
+                           K'_i = (-e^{t_i A} B Q)^T = K_i e^{T A^T}, M' = W and
+                           z0' = e^{TA} z0), so phi, the certified gap and p* (mapped
+                           back) are the same quantities; the iterates differ
+                           and usually need far fewer steps, because the
+                           quadratic term q^T W q is as well conditioned as W
+                           while e^{-TA} W e^{-TA^T} is not.  Inputs (x, p_init)
+                           and p_star stay in the paper's variable.               */
+    int max_steps;      /* hopf_time_to_reach: cap on the candidate horizons solved
+                           per point (0 = 256).  A point still open at the cap
+                           returns T_star = the top of its bracket and the status
+                           HOPF_MAXITER.                                          */
 } hopf_opts;
 
 #define HOPF_KERNEL_AUTO 0
 #define HOPF_KERNEL_GENERIC 1
 
+#define HOPF_VARS_INITIAL 0
+#define HOPF_VARS_TERMINAL 1
+
 /* Fills *opts with the defaults: left Riemann, N = 100 (§VI), max_iter 100000,
  * gap_every 8, FP32, device io, tau 1, sigma_scale 1 (§VI: sigma = 1/(tau |K|^2)),
- * tol_gap 1e-5, t_max 10, tol_T 1e-5, no profiling, accel 0.
+ * tol_gap 1e-5, t_max 10, tol_T 1e-5, no profiling, accel 0, variables
+ * HOPF_VARS_INITIAL.
  * A point counts as converged when its computed relative gap plus an
  * allowance for the rounding of P and D (4 u (|P parts| + |D| + 1) / scale,
  * u the unit roundoff of the iteration's precision) is <= tol_gap. */
@@ -196,6 +216,7 @@ int hopf_value_stacked(const hopf_stacked *prob, const hopf_opts *opts, int P, c
  * candidate horizon is read from the certified interval phi in [-P, -D]; the
  * iteration at that horizon stops as soon as the interval excludes zero.
  *   x        [P*n]
+ *   (opts->tol_T >= 4 DBL_EPSILON; opts->t_max finite and > 0)
  *   T_lo,T_hi NULL, or [P] per-point bracket (warm start: a bracket known to
  *            contain T*; a wrong bracket is detected by the two end-point signs
  *            and replaced by [0, t_max])
@@ -224,6 +245,21 @@ int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P,
 int hopf_trajectory(const hopf_problem *prob, const hopf_opts *opts, int P,
                     const void *x, const void *T, const void *p_star, int S,
                     void *x_traj, void *u_traj, void *stream);
+
+/*
+ * hopf_node_table - the float64 node table that the solves build for one
+ * horizon T (§III.A): node matrices of Eq. 20 generated on the device by
+ * repeated multiplication with e^{-hA} (e^{hA} in terminal-time variables)
+ * and the quadrature weights of Eq. 17 (or of opts->rule).
+ *   K  [N*m*n]  node-major, then control, then state:
+ *               K_i = (-e^{-(T - t_i) A} B Q)^T for HOPF_VARS_INITIAL,
+ *               K'_i = (-e^{t_i A} B Q)^T for HOPF_VARS_TERMINAL
+ *   w  [N]      weights
+ * Device arrays, or host arrays when opts->host_io (then the call waits for
+ * the copy).  T must be finite and >= 0.
+ */
+int hopf_node_table(const hopf_problem *prob, const hopf_opts *opts, double T, double *K, double *w,
+                    void *stream);
 
 /* Human-readable name of a per-point status or a return code. */
 const char *hopf_status_string(int code);
@@ -307,12 +343,14 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
                     int *n_fallback, void *stream);
 
 /*
- * hopf_tc_selftest - diagnostic of the tensor-core primitives used by the
- * large-state kernels (no counterpart in the paper).  One thread block
- * computes D[128][N] = A[128][K] B[N][K]^T with tcgen05.mma of kind::tf32
- * (float32 accumulation in tensor memory) and writes D.  Device arrays,
- * row-major; 16 <= N <= 256 (multiple of 16), 8 <= K <= 128 (multiple of 8).
- * *err (device int) is set to 1 if the completion wait timed out.
+ * hopf_tc_selftest - diagnostic of the library's tcgen05 tensor-core
+ * primitives (shared-memory operand descriptors, instruction descriptor,
+ * tensor-memory accumulator and its read-back), which the warm-start
+ * network's tensor-core prediction uses; no counterpart in the paper.  One
+ * thread block computes D[128][N] = A[128][K] B[N][K]^T with tcgen05.mma of
+ * kind::tf32 (float32 accumulation in tensor memory) and writes D.  Device
+ * arrays, row-major; 16 <= N <= 256 (multiple of 16), 8 <= K <= 128 (multiple
+ * of 8).  *err (device int) is set to 1 if the completion wait timed out.
  */
 int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int *err, void *stream);
 
@@ -333,8 +371,9 @@ int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int
  * Arguments and results are those of hopf_value, with these limits:
  *   - opts->host_io must be 0 (x, t, p_init and outputs are device arrays);
  *   - n <= HOPF_NOALLOC_MAX_N, m <= 16;
+ *   - opts->variables must be HOPF_VARS_INITIAL;
  *   - the scratch the call needs must fit the array, about
- *     8 (n_tables (N m n + N + 4 n^2 + n) + 9 n^2) + P N m sizeof(element)
+ *     8 (n_tables (N m n + N + 6 n^2 + n) + 9 n^2) + P N m sizeof(element)
  *     bytes with n_tables = 1 (t_stride 0) or P (t_stride 1); otherwise the
  *     call returns HOPF_ESCRATCH and does nothing.
  *   Validation failures return the codes of hopf_value; hopf_last_error() is

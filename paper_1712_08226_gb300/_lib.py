@@ -20,7 +20,7 @@ class HopfOpts(ctypes.Structure):
                 ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
                 ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int),
                 ("accel", c_int), ("park_iters", c_int), ("newton", c_int),
-                ("kernel", c_int)]
+                ("kernel", c_int), ("variables", c_int), ("max_steps", c_int)]
 
 
 class HopfMlp(ctypes.Structure):
@@ -36,7 +36,7 @@ class HopfStacked(ctypes.Structure):
 EXPORTS = ("hopf_default_opts", "hopf_value", "hopf_value_stacked", "hopf_time_to_reach", "hopf_trajectory",
            "hopf_status_string", "hopf_last_error", "hopf_release_workspace", "hopf_last_profile",
            "hopf_value_noalloc", "hopf_mlp_param_count", "hopf_mlp_sync", "hopf_mlp_forward",
-           "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm", "hopf_tc_selftest")
+           "hopf_mlp_loss_grad", "hopf_mlp_adam", "hopf_value_warm", "hopf_tc_selftest", "hopf_node_table")
 
 _lib = None
 
@@ -72,6 +72,8 @@ def load(path=LIB_PATH):
     lib.hopf_release_workspace.restype = c_int
     lib.hopf_last_profile.argtypes = [P_double, P_double]
     lib.hopf_last_profile.restype = c_int
+    lib.hopf_node_table.argtypes = [PP, PO, c_double, c_void_p, c_void_p, c_void_p]
+    lib.hopf_node_table.restype = c_int
     lib.hopf_value_noalloc.argtypes = lib.hopf_value.argtypes
     lib.hopf_value_noalloc.restype = c_int
     PM = ctypes.POINTER(HopfMlp)

@@ -14,6 +14,7 @@ from . import _lib
 BALL, BOX = 0, 1
 LEFT_RIEMANN, TRAPEZOID, SIMPSON = 0, 1, 2
 FP64, FP32 = 0, 1
+VARS_INITIAL, VARS_TERMINAL = 0, 1
 STATUS = {0: "ok", 1: "max_iter", 2: "nonfinite", 3: "unreachable", 4: "ambiguous_sign"}
 
 
@@ -67,12 +68,14 @@ class Options:
     park_iters: int = 0
     newton: bool = False
     kernel: int = 0          # 0 auto, 1 force one warp per point
+    variables: int = VARS_INITIAL   # VARS_TERMINAL: iterate in q, p = e^{T A^T} q
+    max_steps: int = 0       # time-to-reach: cap on candidate horizons per point (0 = 256)
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
                              int(self.profile), int(self.accel), int(self.park_iters),
-                             int(self.newton), int(self.kernel))
+                             int(self.newton), int(self.kernel), int(self.variables), int(self.max_steps))
 
 
 def _is_torch(a):
@@ -192,6 +195,27 @@ def time_to_reach(system, x, opts=None, T_lo=None, T_hi=None, p_init=None, strea
     _check(lib, rc)
     out["steps"] = steps.value
     return out
+
+
+def node_table(system, T, opts=None, device=None):
+    """The float64 node table the solves build for horizon T (§III.A, Eq. 20):
+    K (N, m, n) and weights w (N,), in opts.variables.  Host numpy arrays, or
+    float64 torch tensors on `device` when given."""
+    lib = _lib.load()
+    opts = opts or Options()
+    N, m, n = opts.N, system.m, system.n
+    if device is not None:
+        import torch
+        K = torch.empty((N, m, n), dtype=torch.float64, device=device)
+        w = torch.empty((N,), dtype=torch.float64, device=device)
+        s = ctypes.c_void_p(torch.cuda.current_stream(K.device).cuda_stream)
+    else:
+        K, w, s = np.empty((N, m, n)), np.empty(N), None
+    prob = system.c_struct()
+    o = opts.c_struct(device is None)
+    ptr = _Marshal.ptr
+    _check(lib, lib.hopf_node_table(ctypes.byref(prob), ctypes.byref(o), float(T), ptr(K), ptr(w), s))
+    return K, w
 
 
 def last_profile():

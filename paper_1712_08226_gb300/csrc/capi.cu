@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -36,7 +37,13 @@ long long tile_carry_floats(int n, int m, int N, int ppt, int P);
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
-                                       double *out64, float *out32, double *scratch, int need_eig);
+                                       double *out64, float *out32, double *scratch, int need_eig, int terminal);
+template <typename R>
+cudaError_t launch_to_terminal(const double *inst64, int n, int m, int N, int inst_stride, int P, const R *x,
+                               const R *p0, R *xq, R *q0, const int *active, cudaStream_t s);
+template <typename R>
+cudaError_t launch_from_terminal(const double *inst64, int n, int m, int N, int inst_stride, int P, const R *q,
+                                 R *p, const int *active, cudaStream_t s);
 cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                            const double *qd, const double *W, int w_count, const double *Tv,
                                            int n_inst, int n, int m, int N, int rule, double tau,
@@ -69,6 +76,7 @@ template <typename R>
 cudaError_t launch_ttr_update(int P, cudaStream_t s, double t_max, double tol_T, const double *cand,
                               const int *active, const R *Pv, const R *Dv, const int *sst, double *lo,
                               double *hi, int *phase, int *warm, int *st, double *Tfinal, int *remaining);
+cudaError_t launch_ttr_cap(int P, cudaStream_t s, const double *hi, int *phase, int *st, double *Tfinal);
 template <typename R>
 cudaError_t launch_ttr_finish(int P, cudaStream_t s, const int *st, const int *fst, const double *Tfinal,
                               R *T_star, int *status);
@@ -304,6 +312,8 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
         if (o->newton != 0 && o->newton != 1) return fail(HOPF_EINVAL, "newton must be 0 or 1");
         if (o->kernel != HOPF_KERNEL_AUTO && o->kernel != HOPF_KERNEL_GENERIC)
             return fail(HOPF_EINVAL, "kernel must be HOPF_KERNEL_AUTO or HOPF_KERNEL_GENERIC");
+        if (o->variables != HOPF_VARS_INITIAL && o->variables != HOPF_VARS_TERMINAL)
+            return fail(HOPF_EINVAL, "variables must be HOPF_VARS_INITIAL or HOPF_VARS_TERMINAL");
     }
     return HOPF_SUCCESS;
 }
@@ -488,7 +498,8 @@ int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *
                   const int *active, int n_inst, double *inst64, float *inst32, double *scratch, int grid,
                   cudaStream_t s) {
     CU(launch_build_instances_opt(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
-                                  pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch, o->accel));
+                                  pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch, o->accel,
+                                  o->variables == HOPF_VARS_TERMINAL));
     return HOPF_SUCCESS;
 }
 
@@ -520,11 +531,16 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
                                 &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);
     const bool hio = o->host_io != 0;
+    const bool term = o->variables == HOPF_VARS_TERMINAL;
     CarryPair cb;
+    R *xq = nullptr, *q0 = nullptr, *qs = nullptr;
 
     auto plan = [&](Arena &a, DevProblem &d, double *&Tv, double *&i64, float *&i32, double *&tsc,
                     R *&dx, R *&dt, R *&dpi, R *&dphi, R *&dps, R *&dgap, int *&dit, int *&dst, R *&y,
                     int *&ctr, float *&tws, float *&tcs, int *&tcl) {
+        xq = term ? a.template take<R>((size_t)P * n) : nullptr;
+        q0 = (term && pinit_) ? a.template take<R>((size_t)P * n) : nullptr;
+        qs = term ? a.template take<R>((size_t)P * n) : nullptr;
         d = take_problem(a, n, m);
         Tv = a.template take<double>(n_inst);
         i64 = a.template take<double>((size_t)n_inst * L.stride);
@@ -582,6 +598,16 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     rc = launch_tables(d, pr, o, Tv, nullptr, n_inst, i64, i32, tsc, tgrid, s);
     if (rc) return rc;
 
+    // terminal-time variables: the iteration sees e^{TA} x and e^{-TA^T} p_init
+    // and returns q*, mapped back to p* = e^{TA^T} q* after the solve
+    const R *sx = dx, *spi = dpi;
+    R *sps = dps;
+    if (term) {
+        CU(launch_to_terminal<R>(i64, n, m, N, t_stride ? 1 : 0, P, dx, dpi, xq, q0, nullptr, s));
+        sx = xq;
+        spi = q0;
+        sps = qs;
+    }
     if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     SolveParams prm;
     fill_params(prm, pr, o, P);
@@ -589,21 +615,20 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     prm.inst_stride = t_stride ? 1 : 0;
     const R *inst = fp32 ? (const R *)i32 : (const R *)i64;
     if (sp.ok) {
-        rc = run_small_two_phase(sp, sp32, m, (const float *)inst, prm, (const float *)dx, (const float *)dpi,
-                                 (float *)dphi, (float *)dps, (float *)dgap, dit, dst, cb, o->park_iters, s);
+        rc = run_small_two_phase(sp, sp32, m, (const float *)inst, prm, (const float *)sx, (const float *)spi,
+                                 (float *)dphi, (float *)sps, (float *)dgap, dit, dst, cb, o->park_iters, s);
         if (rc) return rc;
     } else if (tile) {
-        CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)dx, (const float *)dpi, (float *)dphi,
-                            (float *)dps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem,
+        CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)sx, (const float *)spi, (float *)dphi,
+                            (float *)sps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem,
                             tile_dbuf, tcs, tcl, s));
     } else {
-        rc = launch_generic<R>(inst, prm, dx, dpi, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
+        rc = launch_generic<R>(inst, prm, sx, spi, dphi, sps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
         if (rc) return rc;
     }
-    if (prof) {
-        CU(cudaEventRecord(g_prof.ev[2], s));
-        g_prof.valid = true;
-    }
+    if (prof) CU(cudaEventRecord(g_prof.ev[2], s));
+    if (term) CU(launch_from_terminal<R>(i64, n, m, N, t_stride ? 1 : 0, P, qs, dps, nullptr, s));
+    if (prof) g_prof.valid = true;
     if (hio) {
         CU(cudaMemcpyAsync(phi_, dphi, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
         CU(cudaMemcpyAsync(pstar_, dps, sizeof(R) * P * n, cudaMemcpyDeviceToHost, s));
@@ -627,6 +652,7 @@ int stacked_impl(const hopf_stacked *sp, const hopf_opts *o, int P, const void *
                  cudaStream_t s) {
     const hopf_problem *pr = &sp->base;
     const int nb = pr->n, m = pr->m, N = o->N, k = sp->copies;
+    if (o->variables != HOPF_VARS_INITIAL) return fail(HOPF_EINVAL, "stacked solve: variables must be HOPF_VARS_INITIAL");
     const bool fp32 = o->precision == HOPF_FP32;
     const int nT = t_stride ? P : 1;
     const int n_inst = nT * k;
@@ -699,8 +725,10 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
         int *phase, *warm, *st, *act, *sst, *fst, *its, *rem;
         R *Pv, *Dv, *phi, *gtmp, *ptmp, *y;
         R *dx, *dlo, *dhi, *dpi, *dTs, *dps, *dgap;
+        R *xq, *q0, *qtmp;   // terminal-time variables: mapped point, warm start, solution
         int *dst;
     } b;
+    const bool term = o->variables == HOPF_VARS_TERMINAL;
     auto plan = [&](Arena &a) {
         b.d = take_problem(a, n, m);
         b.Tz = a.template take<double>(1);
@@ -734,6 +762,9 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
         b.dps = hio ? a.template take<R>((size_t)P * n) : (R *)pstar_;
         b.dgap = hio ? a.template take<R>(P) : (R *)gap_;
         b.dst = hio ? a.template take<int>(P) : status;
+        b.xq = term ? a.template take<R>((size_t)P * n) : nullptr;
+        b.q0 = term ? a.template take<R>((size_t)P * n) : nullptr;
+        b.qtmp = term ? a.template take<R>((size_t)P * n) : nullptr;
     };
     Arena meas(nullptr);
     plan(meas);
@@ -742,6 +773,27 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     if (rc) return rc;
     Arena a(base);
     plan(a);
+    // one solve of the points act (all if null) at the horizons of the current
+    // instances, from p0 (null: cold start), solution into pout; in
+    // terminal-time variables the point and p0 are mapped in and the
+    // solution mapped back
+    auto solve = [&](const SolveParams &pp, const R *inst_, const R *p0, R *pout, R *gout, int *sout,
+                     const int *act) -> int {
+        const R *sx = b.dx, *sp0 = p0;
+        R *sout_p = pout;
+        if (term) {
+            CU(launch_to_terminal<R>(b.i64, n, m, N, 1, P, b.dx, p0, b.xq, p0 ? b.q0 : nullptr, act, s));
+            sx = b.xq;
+            sp0 = p0 ? b.q0 : nullptr;
+            sout_p = b.qtmp;
+        }
+        SolveParams q = pp;
+        q.warm = sp0 != nullptr;
+        int r = launch_generic<R>(inst_, q, sx, sp0, b.phi, sout_p, gout, b.its, sout, b.Pv, b.Dv, b.y, act, s);
+        if (r) return r;
+        if (term) CU(launch_from_terminal<R>(b.i64, n, m, N, 1, P, b.qtmp, pout, act, s));
+        return HOPF_SUCCESS;
+    };
 
     rc = upload_problem(b.d, pr, s);
     if (rc) return rc;
@@ -765,7 +817,8 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     prm.inst_stride = 1;
     const R *inst = fp32 ? (const R *)b.i32 : (const R *)b.i64;
     int steps = 0;
-    const int max_steps = 256;
+    const int max_steps = o->max_steps > 0 ? o->max_steps : 256;
+    int remaining = 0;
     if (o->newton) {
         // hybrid Newton/bisection (§IV).  A candidate's solve stops as soon as
         // the sign of phi is certified (or at tol_gap); the step uses the
@@ -779,15 +832,12 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
             rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
             if (rc) return rc;
             const R *p0 = steps == 0 ? b.dpi : b.ptmp;
-            prm.warm = p0 != nullptr;
-            rc = launch_generic<R>(inst, prm, b.dx, p0, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
-                                   b.act, s);
+            rc = solve(prm, inst, p0, b.ptmp, b.gtmp, b.sst, b.act);
             if (rc) return rc;
             CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
             CU(launch_ttr_newton_update<R>(P, s, n, m, pr->ctrl_kind, b.d.A, b.d.B, b.d.q, b.dx, o->t_max, o->tol_T,
                                            b.Pv, b.Dv, b.ptmp, b.cand, b.act, b.lo, b.hi, b.phase, b.st, b.Tf,
                                            b.rem));
-            int remaining = 0;
             CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             ++steps;
@@ -800,24 +850,23 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
         rc = launch_tables(b.d, pr, o, b.cand, b.act, P, b.i64, b.i32, b.tsc, tgrid, s);
         if (rc) return rc;
         prm.sign_mode = 1;
-        rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.ptmp, b.gtmp, b.its, b.sst, b.Pv, b.Dv, b.y,
-                               b.act, s);
+        rc = solve(prm, inst, b.dpi, b.ptmp, b.gtmp, b.sst, b.act);
         if (rc) return rc;
         CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
         CU(launch_ttr_update<R>(P, s, o->t_max, o->tol_T, b.cand, b.act, b.Pv, b.Dv, b.sst, b.lo, b.hi, b.phase,
                                 b.warm, b.st, b.Tf, b.rem));
-        int remaining = 0;
         CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         ++steps;
         if (remaining == 0 || steps >= max_steps) break;
     }
+    // points the step cap stopped: T* = top of the bracket, status MAXITER
+    if (remaining > 0) CU(launch_ttr_cap(P, s, b.hi, b.phase, b.st, b.Tf));
     // final certified solve at T* (T = 0 inside the target, t_max if unreachable)
     rc = launch_tables(b.d, pr, o, b.Tf, nullptr, P, b.i64, b.i32, b.tsc, tgrid, s);
     if (rc) return rc;
     prm.sign_mode = 0;
-    rc = launch_generic<R>(inst, prm, b.dx, b.dpi, b.phi, b.dps, b.dgap, b.its, b.fst, b.Pv, b.Dv, b.y,
-                           nullptr, s);
+    rc = solve(prm, inst, b.dpi, b.dps, b.dgap, b.fst, nullptr);
     if (rc) return rc;
     CU(launch_ttr_finish<R>(P, s, b.st, b.fst, b.Tf, b.dTs, b.dst));
     if (hio) {
@@ -893,6 +942,37 @@ int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_,
     return HOPF_SUCCESS;
 }
 
+// ------------------------------------------------------- hopf_node_table
+int node_table_impl(const hopf_problem *pr, const hopf_opts *o, double T, double *K_, double *w_, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    DevProblem d;
+    double *Tv, *i64, *tsc;
+    auto plan = [&](Arena &a) {
+        d = take_problem(a, n, m);
+        Tv = a.template take<double>(1);
+        i64 = a.template take<double>((size_t)L.stride);
+        tsc = a.template take<double>((size_t)table_scratch_doubles(n, m));
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    int rc = ensure_workspace(meas.off, &base, s);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    rc = upload_problem(d, pr, s);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(Tv, &T, sizeof(double), cudaMemcpyHostToDevice, s));
+    rc = launch_tables(d, pr, o, Tv, nullptr, 1, i64, nullptr, tsc, 1, s);
+    if (rc) return rc;
+    const cudaMemcpyKind kind = o->host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CU(cudaMemcpyAsync(K_, i64 + L.K, sizeof(double) * (size_t)N * m * n, kind, s));
+    CU(cudaMemcpyAsync(w_, i64 + L.w, sizeof(double) * (size_t)N, kind, s));
+    if (o->host_io) CU(cudaStreamSynchronize(s));
+    return HOPF_SUCCESS;
+}
+
 // network prediction: tensor cores when requested and the layers fit one MMA in N
 int net_predict(const hopf_mlp *net, int B, const float *x, float *y, float *scratch, int *err, cudaStream_t s) {
     if (net->use_tc && net->hidden <= 256 && net->n_out <= 256) {
@@ -943,10 +1023,15 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     int *list, *cnt, *ctr, *ord, *obucket, *ocount, *ototal;
     CarryPair cb;
     const bool hio = o->host_io != 0;
+    const bool term = o->variables == HOPF_VARS_TERMINAL;
     float *dx, *dt, *dphi, *dps, *dgap;
+    float *xq = nullptr, *qhat = nullptr, *qs = nullptr;
     int *dit, *dst;
     auto plan = [&](Arena &a) {
         d = take_problem(a, n, m);
+        xq = term ? a.template take<float>((size_t)P * n) : nullptr;
+        qhat = term ? a.template take<float>((size_t)P * n) : nullptr;
+        qs = term ? a.template take<float>((size_t)P * n) : nullptr;
         dx = hio ? a.template take<float>((size_t)P * n) : (float *)x_;
         dt = hio ? a.template take<float>((size_t)n_inst) : (float *)t_;
         dphi = hio ? a.template take<float>(P) : (float *)phi_;
@@ -1013,28 +1098,29 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     SolveParams prm;
     fill_params(prm, pr, o, P);
     prm.inst_stride = t_stride ? 1 : 0;
+    // in terminal-time variables the solves see e^{TA} x and q = e^{-TA^T} p
+    const float *sx = term ? xq : dx;
+    float *sps = term ? qs : dps;
     auto solve = [&](const SolveParams &pp, const float *pinit) -> int {
         if (sp.ok)
-            return run_small_two_phase(sp, sp32, m, i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, cb,
+            return run_small_two_phase(sp, sp32, m, i32, pp, sx, pinit, dphi, sps, dgap, dit, dst, cb,
                                        o->park_iters, s);
         if (tile) {
-            CU(launch_pdhg_tile(i32, i64, pp, dx, pinit, dphi, dps, dgap, dit, dst, tws, ctr, tile_ppt, tile_grid,
+            CU(launch_pdhg_tile(i32, i64, pp, sx, pinit, dphi, sps, dgap, dit, dst, tws, ctr, tile_ppt, tile_grid,
                                 tile_smem, tile_dbuf, tcs, tcl, s));
             return HOPF_SUCCESS;
         }
-        return launch_generic<float>(i32, pp, dx, pinit, dphi, dps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
+        return launch_generic<float>(i32, pp, sx, pinit, dphi, sps, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
     };
-    // hardest-first order of the warm solve; the hardest points (one wave of
-    // the 32-lane kernel on a quarter of the SMs) run concurrently with the rest
-    const bool split = false;
-    const int g_hard = split ? std::max(1, dev.sms / 4) : 0;
-    const int n_hard = split ? std::min(P, g_hard * sp32.pts) : 0;
+    // hardest-first order of the warm solve
     CU(cudaMemsetAsync(ocount, 0, sizeof(int) * ORDER_BUCKETS, s));
     order_count_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, n, phat, obucket, ocount);
-    order_scan_kernel<<<1, 32, 0, s>>>(P, n_hard, ocount, ototal);
+    order_scan_kernel<<<1, 32, 0, s>>>(P, 0, ocount, ototal);
     order_scatter_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, obucket, ocount, ord);
     CU(cudaGetLastError());
     CU(cudaStreamWaitEvent(s, tsd->join, 0));
+    if (term) CU(launch_to_terminal<float>(i64, n, m, N, t_stride ? 1 : 0, P, dx, phat, xq, qhat, nullptr, s));
+    const float *pstart = term ? qhat : phat;
     if (prof) CU(cudaEventRecord(g_prof.ev[1], s));
     // warm solve, capped at max_iter_warm
     SolveParams pw = prm;
@@ -1042,31 +1128,8 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
     pw.max_iter = max_iter_warm;
     pw.list = ord;
     pw.list_count = ototal;
-    if (split) {
-        Side *sd = nullptr;
-        rc = side_stream(dev.id, &sd);
-        if (rc) return rc;
-        CU(cudaMemsetAsync(ctr + 1, 0, sizeof(int), s));
-        CU(cudaEventRecord(sd->fork, s));
-        CU(cudaStreamWaitEvent(sd->stream, sd->fork, 0));
-        SolveParams ph = pw;                       // hardest points, 32 lanes each
-        ph.list_count = ototal + 1;
-        ph.carry_cap = 0;
-        CU(launch_pdhg_small(sp32.NS, m, 32, g_hard, sp32.threads, sp32.smem, sd->stream, i32, ph, sp32.ys_stride,
-                             dx, phat, dphi, dps, dgap, dit, dst, ctr + 1));
-        SolveParams pe = pw;                       // the rest, 4 lanes each, parking slow ones
-        pe.list = ord + n_hard;
-        pe.list_count = ototal + 2;
-        SmallPlan spe = sp;
-        spe.grid = std::max(1, dev.sms - g_hard);
-        rc = run_small_two_phase(spe, sp32, m, i32, pe, dx, phat, dphi, dps, dgap, dit, dst, cb, o->park_iters, s);
-        if (rc) return rc;
-        CU(cudaEventRecord(sd->join, sd->stream));
-        CU(cudaStreamWaitEvent(s, sd->join, 0));
-    } else {
-        rc = solve(pw, phat);
-        if (rc) return rc;
-    }
+    rc = solve(pw, pstart);
+    if (rc) return rc;
     // cold fallback for every point that the warm solve did not certify
     CU(cudaMemsetAsync(cnt, 0, sizeof(int), s));
     failed_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dst, list, cnt);
@@ -1081,6 +1144,7 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         CU(cudaEventRecord(g_prof.ev[2], s));
         g_prof.valid = true;
     }
+    if (term) CU(launch_from_terminal<float>(i64, n, m, N, t_stride ? 1 : 0, P, qs, dps, nullptr, s));
     if (n_fallback)
         CU(cudaMemcpyAsync(n_fallback, cnt, sizeof(int), hio ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     if (hio) {
@@ -1173,7 +1237,10 @@ int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P, c
     if (P < 0) return fail(HOPF_EINVAL, "P must be >= 0");
     if (steps) *steps = 0;
     if (P == 0) return HOPF_SUCCESS;
-    if (!(opts->t_max > 0.0) || !(opts->tol_T > 0.0)) return fail(HOPF_EINVAL, "need t_max > 0 and tol_T > 0");
+    if (!(opts->t_max > 0.0) || !std::isfinite(opts->t_max)) return fail(HOPF_EINVAL, "need finite t_max > 0");
+    // below a few float64 ulps the bracket test hi - lo <= tol_T hi can never hold
+    if (!(opts->tol_T >= 4.0 * DBL_EPSILON)) return fail(HOPF_EINVAL, "need tol_T >= 4 DBL_EPSILON");
+    if (opts->max_steps < 0) return fail(HOPF_EINVAL, "need max_steps >= 0");
     if ((T_lo == nullptr) != (T_hi == nullptr)) return fail(HOPF_EINVAL, "give both T_lo and T_hi or neither");
     if (!x || !T_star || !p_star || !gap || !status) return fail(HOPF_EINVAL, "null array");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1195,6 +1262,16 @@ int hopf_trajectory(const hopf_problem *prob, const hopf_opts *opts, int P, cons
     if (opts->precision == HOPF_FP64)
         return traj_impl<double>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
     return traj_impl<float>(prob, opts, P, x, T, p_star, S, x_traj, u_traj, s);
+}
+
+int hopf_node_table(const hopf_problem *prob, const hopf_opts *opts, double T, double *K, double *w, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    int rc = check_problem(prob, opts, true);
+    if (rc) return rc;
+    if (!(T >= 0.0) || !std::isfinite(T)) return fail(HOPF_EINVAL, "T must be finite and >= 0");
+    if (!K || !w) return fail(HOPF_EINVAL, "null array");
+    return node_table_impl(prob, opts, T, K, w, (cudaStream_t)stream);
 }
 
 long long hopf_mlp_param_count(int n_in, int hidden, int n_out) { return mlp_param_count(n_in, hidden, n_out); }

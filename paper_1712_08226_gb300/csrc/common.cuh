@@ -9,7 +9,11 @@
 //   S    [n][n]     (I + tau M / 2)^-1                          (Eq. 37)
 //   U    [n][n]     eigenvectors of M (M = U diag(lam) U^T), for the
 //   lam  [n]        accelerated iteration whose step tau changes every step
+//   E    [n][n]     e^{TA}: maps the query point to the terminal-time variable
+//   Ei   [n][n]     e^{-TA}  (both the identity for the paper's variable)
 //   sc   [8]        sigma, T, |K|^2, flag (1 = T == 0), gamma = lambda_min(M)/2
+// In terminal-time variables (p = e^{T A^T} q) the same slots hold
+// K'_i = (-e^{t_i A} B Q)^T, M' = W, V' = W^-1, S' = (I + tau W/2)^-1.
 // A float32 copy with the same layout is made for the float32 kernels.
 #pragma once
 #include <cuda_runtime.h>
@@ -21,7 +25,7 @@ namespace hopf {
 
 struct InstanceLayout {
     // element offsets (in elements of the instance's type) inside one instance
-    long long K, w, M, V, S, U, lam, sc, stride;
+    long long K, w, M, V, S, U, lam, E, Ei, sc, stride;
     __host__ __device__ static InstanceLayout make(int n, int m, int N) {
         InstanceLayout L;
         long long o = 0;
@@ -33,6 +37,8 @@ struct InstanceLayout {
         L.S = o;  o = al(o + (long long)n * n);
         L.U = o;  o = al(o + (long long)n * n);
         L.lam = o; o = al(o + n);
+        L.E = o;  o = al(o + (long long)n * n);
+        L.Ei = o; o = al(o + (long long)n * n);
         L.sc = o; o = al(o + 8);
         L.stride = o;
         return L;

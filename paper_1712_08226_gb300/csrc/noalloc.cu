@@ -28,6 +28,7 @@
 //  * sizes that do not fit the array are rejected with HOPF_ESCRATCH.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -49,18 +50,20 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HOPF_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// one cached address per device; host threads making their first call on the
+// same device at once may both look it up, and both store the same value
+std::atomic<void *> g_scratch_ptr[kMaxDevices];
 
 // Device address of the static array for the current device (looked up once).
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HOPF_ECUDA;
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
+    void *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HOPF_ECUDA;
-        g_scratch_ptr[dev] = p;
+        g_scratch_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return HOPF_SUCCESS;
 }
 
@@ -125,6 +128,7 @@ int validate(const hopf_problem *pr, const hopf_opts *o) {
     if (!(o->tau > 0.0) || !(o->sigma_scale > 0.0) || !(o->sigma_scale <= 1.0)) return HOPF_EINVAL;
     if (!(o->tol_gap >= 0.0)) return HOPF_EINVAL;
     if (o->accel != 0 && o->accel != 1) return HOPF_EINVAL;
+    if (o->variables != HOPF_VARS_INITIAL) return HOPF_EINVAL;   // the paper's variable only
     return HOPF_SUCCESS;
 }
 

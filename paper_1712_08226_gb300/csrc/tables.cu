@@ -13,6 +13,13 @@
 // eigenvalue is |K|^2 for the dual step sigma = 1/(tau |K|^2) of §VI.
 // The quadratic target of §VI.A needs M = V(0)^-1 = e^{-TA} W e^{-TA^T}
 // (Eq. 35), V = M^-1 and the prox matrix S = (I + tau M/2)^-1 (Eq. 37).
+//
+// Terminal-time variables (terminal != 0): with p = e^{T A^T} q every term of
+// Eq. 18 keeps its form with K'_i = K_i e^{T A^T} = (-e^{t_i A} B Q)^T,
+// M' = W, V' = W^-1, S' = (I + tau W/2)^-1 and the query point mapped to
+// e^{TA} z0.  K'_i is generated the same way, by repeated multiplication
+// with e^{hA} from t_0 = 0.  E = e^{TA} and Ei = e^{-TA} are stored for the
+// maps of the query point and of p (identity in the paper's variable).
 #include "common.cuh"
 #include "cta_linalg.cuh"
 
@@ -23,7 +30,8 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                                        const double *__restrict__ Tv, const int *__restrict__ active,
                                        int n_inst, int n, int m, int N, int rule, double tau,
                                        double sigma_scale, double *out64, float *out32,
-                                       double *scratch, bool smem_scratch, int w_count, int need_eig) {
+                                       double *scratch, bool smem_scratch, int w_count, int need_eig,
+                                       int terminal) {
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     // scratch in shared memory when the launch provides it (small n), else global
     extern __shared__ double tsm[];
@@ -43,18 +51,20 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         const bool ends = rule == HOPF_TRAPEZOID || rule == HOPF_SIMPSON;   // samples include t = T
         const double h = ends ? T / (double)(N - 1) : T / (double)N;
 
-        cta::expm(Eh, A, -h, n, X, T1, red);
+        cta::expm(Eh, A, terminal ? h : -h, n, X, T1, red);
         // G = B Q, Gram accumulator C = 0
         for (int e = threadIdx.x; e < n * m; e += blockDim.x) Ga[e] = B[e] * qd[e % m];
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) C[e] = 0.0;
         __syncthreads();
         double *cur = Ga, *nxt = Gb;
         for (int idx = 0; idx < N; ++idx) {
-            if (!ends || idx > 0) {
-                cta::matmul(nxt, Eh, cur, n, n, m);     // advance s by h
+            if (terminal ? idx > 0 : (!ends || idx > 0)) {
+                cta::matmul(nxt, Eh, cur, n, n, m);     // advance s (or t) by h
                 double *t = cur; cur = nxt; nxt = t;
             }
-            const int i = N - 1 - idx;                  // node with s_i = (idx + [left]) h
+            // paper's variable: node with s_i = (idx + [left]) h; terminal
+            // variables: node idx at t = idx h
+            const int i = terminal ? idx : N - 1 - idx;
             double *Ki = o + L.K + (long long)i * m * n;
             for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
                 int c = e / n, j = e % n;
@@ -74,10 +84,17 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
             if (rule == HOPF_SIMPSON) wi = (i == 0 || i == N - 1) ? h / 3.0 : ((i & 1) ? 4.0 * h / 3.0 : 2.0 * h / 3.0);
             o[L.w + i] = wi;
         }
-        // M = e^{-TA} W e^{-TA}^T (symmetrised), V = M^-1, S = (I + tau M / 2)^-1
+        // M = e^{-TA} W e^{-TA}^T (symmetrised; W itself in terminal-time
+        // variables), V = M^-1, S = (I + tau M / 2)^-1
         cta::expm(ET, A, -T, n, X, T1, red);
-        cta::matmul(T2, ET, W + (long long)(inst % w_count) * n * n, n, n, n);
-        cta::matmul_bt(T1, T2, ET, n, n, n);
+        const double *Wk = W + (long long)(inst % w_count) * n * n;
+        if (terminal) {
+            cta::copy(o + L.Ei, ET, n * n);
+            cta::copy(T1, Wk, n * n);
+        } else {
+            cta::matmul(T2, ET, Wk, n, n, n);
+            cta::matmul_bt(T1, T2, ET, n, n, n);
+        }
         double *Mo = o + L.M, *Vo = o + L.V, *So = o + L.S;
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             int a = e / n, b = e % n;
@@ -95,6 +112,19 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
         bool okS = cta::invert(T2, X, n, Aug, piv, red);
         for (int e = threadIdx.x; e < n * n; e += blockDim.x)
             So[e] = okS ? T2[e] : __longlong_as_double(0x7ff8000000000000LL);
+        __syncthreads();
+        // maps of the query point and of p: e^{TA}, e^{-TA} (identity in the
+        // paper's variable)
+        if (terminal) {
+            cta::expm(T2, A, T, n, X, T1, red);
+            cta::copy(o + L.E, T2, n * n);
+        } else {
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+                const double id = (e / n == e % n) ? 1.0 : 0.0;
+                o[L.E + e] = id;
+                o[L.Ei + e] = id;
+            }
+        }
         __syncthreads();
         // |K|^2 = largest eigenvalue of the Gram matrix: Jacobi for small n
         // (a few hundred block barriers), the power method otherwise
@@ -162,21 +192,21 @@ cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const 
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
                                                                       tau, sigma_scale, out64, out32, scratch, in_smem, 1,
-                                                                      1);
+                                                                      1, 0);
     return cudaGetLastError();
 }
 
 // as launch_build_instances, with the eigen-decomposition of M (used only by
-// the accelerated iteration) optional
+// the accelerated iteration) optional and the choice of variables
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
-                                       double *out64, float *out32, double *scratch, int need_eig) {
+                                       double *out64, float *out32, double *scratch, int need_eig, int terminal) {
     const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
                                                                       tau, sigma_scale, out64, out32, scratch, in_smem, 1,
-                                                                      need_eig);
+                                                                      need_eig, terminal);
     return cudaGetLastError();
 }
 
@@ -189,7 +219,7 @@ cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, nullptr, n_inst, n, m, N,
                                                                       rule, tau, sigma_scale, out64, out32, scratch,
-                                                                      in_smem, w_count, 0);
+                                                                      in_smem, w_count, 0, 0);
     return cudaGetLastError();
 }
 

@@ -38,8 +38,19 @@ __global__ void ttr_init_kernel(const double *__restrict__ inst0, int n, int m, 
     if (!(l >= 0.0) || !(h > l) || !(h <= t_max)) { wb = false; l = 0.0; h = t_max; }
     lo[k] = l;
     hi[k] = h;
+    Tfinal[k] = h;     // replaced when the point finishes; kept if the step cap stops it first
     warm[k] = wb ? 1 : 0;
     phase[k] = PH_HI;
+}
+
+// Step cap reached: every point still open gets the top of its bracket as
+// T* (the final solve there gives p*) and the status HOPF_MAXITER.
+__global__ void ttr_cap_kernel(int P, const double *hi, int *phase, int *st, double *Tfinal) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P || phase[k] == PH_DONE) return;
+    phase[k] = PH_DONE;
+    Tfinal[k] = hi[k];
+    st[k] = HOPF_MAXITER;
 }
 
 __global__ void ttr_candidates_kernel(int P, const double *lo, const double *hi, const int *phase,
@@ -305,6 +316,11 @@ cudaError_t launch_ttr_newton_update(int P, cudaStream_t s, int n, int m, int ct
     ttr_newton_update_kernel<R><<<(P + 127) / 128, 128, 0, s>>>(P, n, m, ctrl_kind, A, B, qd, x, t_max, tol_T, Pv,
                                                                 Dv, pstar, cand, active, lo, hi, phase, st, Tfinal,
                                                                 remaining);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ttr_cap(int P, cudaStream_t s, const double *hi, int *phase, int *st, double *Tfinal) {
+    ttr_cap_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, hi, phase, st, Tfinal);
     return cudaGetLastError();
 }
 

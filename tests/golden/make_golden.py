@@ -95,8 +95,42 @@ def unscented_time_to_reach(P=3):
          T=r["T"], p=r["p"], status=r["status"])
 
 
+def chain_values(P=32, stride=4, T=10.0):
+    # the 100-mass spring chain at full size (n = 200, m = 10 box, N = 512):
+    # every stride-th of the first P seeded points.  The oracle runs in
+    # terminal-time variables (the same phi; pinned like the paper's form)
+    # because the paper's variable needs ~20x more iterations at this size.
+    w = wl.workload_chain(P)
+    idx = np.arange(0, P, stride)
+    r = oh.value(w["system"], w["x"][idx], T, w["N"], w["rule"], tau=0.1, tol=1e-7, max_iter=2000000,
+                 variables="terminal")
+    assert np.all(r["status"] == oh.OK)
+    dump("chain200_values_T10.json",
+         dict(source="oracle.hopf.value (variables=terminal)",
+              workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, points idx of the first P",
+              P=P, T=T, N=w["N"], rule="left_riemann", tau=0.1, oracle_tol=1e-7),
+         idx=idx, phi=r["phi"], p=r["p"], gap=r["gap"])
+
+
+def random128_values(P=8):
+    # the largest size of the 64 random systems: n = 128, m = ceil(n/8) = 16
+    sysd = wl.random_system(328, 128, 16)
+    x = wl.normal_points(428, P, 128, 2.0)
+    r = oh.value(sysd, x, 2.0, 256, oh.LEFT_RIEMANN, tau=0.15, tol=1e-8, max_iter=2000000, variables="terminal")
+    assert np.all(r["status"] == oh.OK)
+    dump("random128_values.json",
+         dict(source="oracle.hopf.value (variables=terminal)",
+              workload="random system seed 328 (n=128, m=16 ball), x~N(0,4I) seed 428", P=P, T=2.0, N=256,
+              rule="left_riemann", tau=0.15, oracle_tol=1e-8),
+         phi=r["phi"], p=r["p"], gap=r["gap"])
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["random10", "di", "ttr", "box", "chain10", "unscented"]
+    which = sys.argv[1:] or ["random10", "di", "ttr", "box", "chain10", "unscented", "chain200", "random128"]
+    if "chain200" in which:
+        chain_values()
+    if "random128" in which:
+        random128_values()
     if "unscented" in which:
         unscented_time_to_reach()
     if "chain10" in which:

@@ -149,3 +149,20 @@ def test_trained_warm_start_beats_cold_start(H):
     it_c = cold["iters"].float().mean().item()
     it_w = warm["iters"].float().mean().item()
     assert it_w < 0.8 * it_c, (it_w, it_c)
+    # the warm-started values against the FP64 oracle directly, on a sample
+    from oracle import hopf as oh
+    idx = np.random.default_rng(16).choice(4096, 16, replace=False)
+    xs = wl.normal_points(41, 4096, 10, 2.0)[idx]
+    ref = oh.value(w["system"], xs, 2.0, 256, oh.LEFT_RIEMANN, tau=0.15, tol=1e-10, max_iter=400000)
+    assert np.max(np.abs(phi_w[idx] - ref["phi"]) / np.maximum(1.0, np.abs(ref["phi"]))) <= 1e-5
+    # the same network warm-starting the solve in terminal-time variables: the
+    # prediction of p* is mapped to q, the values are the oracle's
+    opts_t = H.Options(N=256, tau=0.5, tol_gap=1e-5, variables=1)
+    warm_t = value_warm(sysd, xte, 2.0, net, opts_t, max_iter_warm=2000)
+    cold_t = H.value(sysd, xte, 2.0, opts_t)
+    assert np.all(warm_t["status"].cpu().numpy() == 0)
+    phi_t = warm_t["phi"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(phi_t[idx] - ref["phi"]) / np.maximum(1.0, np.abs(ref["phi"]))) <= 1e-5
+    # (this small network's prediction is too coarse to shorten the ~80-step
+    # terminal-variable solves much; the benchmark's trained network does)
+    assert warm_t["iters"].float().mean().item() < 1.25 * cold_t["iters"].float().mean().item()
