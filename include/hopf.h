@@ -128,7 +128,13 @@ typedef struct {
     int kernel;         /* hopf_value solve kernel: HOPF_KERNEL_AUTO (0) picks by
                            size; HOPF_KERNEL_GENERIC (1) forces one warp per
                            point (the reference layout of the iteration; used
-                           to compare the specialised kernels with it).          */
+                           to compare the specialised kernels with it);
+                           HOPF_KERNEL_TENSOR (2) asks for the tensor-core
+                           kernel wherever it applies (float32, one horizon,
+                           terminal-time variables, diagonal W, accel 0,
+                           16 <= n <= 256), else AUTO's choice among the others;
+                           HOPF_KERNEL_TILE (3) the CUDA-core tiled kernel for
+                           large states.                                          */
     int variables;      /* variable the iteration of Eq. 15 runs in.
                            HOPF_VARS_INITIAL (0): the paper's p of Eq. 18.
                            HOPF_VARS_TERMINAL (1): q with p = e^{T A^T} q (the
@@ -149,6 +155,8 @@ typedef struct {
 
 #define HOPF_KERNEL_AUTO 0
 #define HOPF_KERNEL_GENERIC 1
+#define HOPF_KERNEL_TENSOR 2
+#define HOPF_KERNEL_TILE 3
 
 #define HOPF_VARS_INITIAL 0
 #define HOPF_VARS_TERMINAL 1

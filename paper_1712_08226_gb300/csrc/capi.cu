@@ -34,6 +34,11 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
                              float *ws, int *queue, int ppt, int grid, size_t smem, int dbuf, float *carry_st,
                              int *carry_list, cudaStream_t s);
 long long tile_carry_floats(int n, int m, int N, int ppt, int P);
+bool tc_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *grid);
+long long tc_workspace_floats(int n, int m, int N, int grid);
+cudaError_t launch_pdhg_tc(const float *inst, const double *inst64, const SolveParams &prm, const float *x,
+                           const float *p_init, float *phi, float *pstar, float *gap, int *iters, int *status, float *ws,
+                           int *queue, int grid, cudaStream_t s);
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
@@ -310,8 +315,9 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
         if (!(o->tol_gap >= 0.0)) return fail(HOPF_EINVAL, "bad tol_gap");
         if (o->accel != 0 && o->accel != 1) return fail(HOPF_EINVAL, "accel must be 0 or 1");
         if (o->newton != 0 && o->newton != 1) return fail(HOPF_EINVAL, "newton must be 0 or 1");
-        if (o->kernel != HOPF_KERNEL_AUTO && o->kernel != HOPF_KERNEL_GENERIC)
-            return fail(HOPF_EINVAL, "kernel must be HOPF_KERNEL_AUTO or HOPF_KERNEL_GENERIC");
+        if (o->kernel != HOPF_KERNEL_AUTO && o->kernel != HOPF_KERNEL_GENERIC && o->kernel != HOPF_KERNEL_TENSOR &&
+            o->kernel != HOPF_KERNEL_TILE)
+            return fail(HOPF_EINVAL, "kernel must be one of HOPF_KERNEL_AUTO, _GENERIC, _TENSOR, _TILE");
         if (o->variables != HOPF_VARS_INITIAL && o->variables != HOPF_VARS_TERMINAL)
             return fail(HOPF_EINVAL, "variables must be HOPF_VARS_INITIAL or HOPF_VARS_TERMINAL");
     }
@@ -505,6 +511,25 @@ int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *
 
 int table_grid(const Device &dev, int n_inst) { return std::max(1, std::min(n_inst, 4 * dev.sms)); }
 
+bool diagonal(const double *W, int n) {
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            if (a != b && W[a * n + b] != 0.0) return false;
+    return true;
+}
+
+// The tensor-core kernel: float32, one shared table, terminal-time variables
+// with a diagonal W (diagonal M', V', S'), plain steps (Eq. 15), 16 <= n <= 256.
+// Chosen automatically when the batch fills at least half of the SMs with
+// 128-point tiles; HOPF_KERNEL_TENSOR asks for it whenever it applies.
+bool want_tc(const hopf_problem *pr, const hopf_opts *o, int t_stride, int P, const Device &dev, int *grid) {
+    if (o->precision != HOPF_FP32 || t_stride != 0 || o->accel || o->variables != HOPF_VARS_TERMINAL) return false;
+    if (o->kernel != HOPF_KERNEL_AUTO && o->kernel != HOPF_KERNEL_TENSOR) return false;
+    if (o->kernel == HOPF_KERNEL_AUTO && (pr->n < 32 || P < 64 * dev.sms)) return false;
+    if (!diagonal(pr->W, pr->n)) return false;
+    return tc_plan(pr->n, pr->m, o->N, P, dev.sms, dev.smem_optin - 2048, grid);
+}
+
 // --------------------------------------------------------------- hopf_value
 template <typename R>
 int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *t_,
@@ -523,10 +548,13 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         sp32 = plan_small(dev, n, m, N, P, 32);
         sp32.grid = dev.sms;
     }
-    // large states, one shared table: the tiled kernel
+    // large states, one shared table: the tensor-core kernel or the tiled kernel
+    int tc_grid = 0;
+    const bool tcore = !sp.ok && want_tc(pr, o, t_stride, P, dev, &tc_grid);
     int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
     size_t tile_smem = 0;
-    const bool tile = fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !sp.ok &&
+    const bool tile = fp32 && t_stride == 0 && !tcore && !sp.ok &&
+                      (o->kernel == HOPF_KERNEL_AUTO || o->kernel == HOPF_KERNEL_TILE) &&
                       tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
                                 &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);
@@ -554,9 +582,10 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         dgap = hio ? a.template take<R>(P) : (R *)gap_;
         dit = hio ? a.template take<int>(P) : iters;
         dst = hio ? a.template take<int>(P) : status;
-        y = (sp.ok || tile) ? nullptr : a.template take<R>((size_t)P * N * m);
+        y = (sp.ok || tile || tcore) ? nullptr : a.template take<R>((size_t)P * N * m);
         ctr = a.template take<int>(4);
-        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid))
+                   : (tcore ? a.template take<float>((size_t)tc_workspace_floats(n, m, N, tc_grid)) : nullptr);
         tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
         tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
@@ -618,6 +647,9 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
         rc = run_small_two_phase(sp, sp32, m, (const float *)inst, prm, (const float *)sx, (const float *)spi,
                                  (float *)dphi, (float *)sps, (float *)dgap, dit, dst, cb, o->park_iters, s);
         if (rc) return rc;
+    } else if (tcore) {
+        CU(launch_pdhg_tc((const float *)inst, i64, prm, (const float *)sx, (const float *)spi, (float *)dphi,
+                          (float *)sps, (float *)dgap, dit, dst, tws, ctr, tc_grid, s));
     } else if (tile) {
         CU(launch_pdhg_tile((const float *)inst, i64, prm, (const float *)sx, (const float *)spi, (float *)dphi,
                             (float *)sps, (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem,
