@@ -1041,10 +1041,13 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         sp32 = plan_small(dev, n, m, N, P, 32);
         sp32.grid = dev.sms;
     }
-    // large states, one shared table: the tiled kernel (warm solve and fallback)
+    // large states, one shared table: the tensor-core or the tiled kernel
+    // (warm solve and fallback)
+    int tc_grid = 0;
+    const bool tcore = !sp.ok && want_tc(pr, o, t_stride, P, dev, &tc_grid);
     int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
     size_t tile_smem = 0;
-    const bool tile = t_stride == 0 && !sp.ok &&
+    const bool tile = t_stride == 0 && !sp.ok && !tcore &&
                       tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
                                 &tile_dbuf);
     const int tgrid = table_grid(dev, n_inst);
@@ -1084,8 +1087,9 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         obucket = a.template take<int>(P);
         ocount = a.template take<int>(ORDER_BUCKETS);
         ototal = a.template take<int>(4);
-        y = (sp.ok || tile) ? nullptr : a.template take<float>((size_t)P * N * m);
-        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        y = (sp.ok || tile || tcore) ? nullptr : a.template take<float>((size_t)P * N * m);
+        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid))
+                   : (tcore ? a.template take<float>((size_t)tc_workspace_floats(n, m, N, tc_grid)) : nullptr);
         tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
         tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
         if (sp.ok) cb = take_carry(a, P, N, m);
@@ -1137,6 +1141,10 @@ int value_warm_impl(const hopf_problem *pr, const hopf_opts *o, const hopf_mlp *
         if (sp.ok)
             return run_small_two_phase(sp, sp32, m, i32, pp, sx, pinit, dphi, sps, dgap, dit, dst, cb,
                                        o->park_iters, s);
+        if (tcore) {
+            CU(launch_pdhg_tc(i32, i64, pp, sx, pinit, dphi, sps, dgap, dit, dst, tws, ctr, tc_grid, s));
+            return HOPF_SUCCESS;
+        }
         if (tile) {
             CU(launch_pdhg_tile(i32, i64, pp, sx, pinit, dphi, sps, dgap, dit, dst, tws, ctr, tile_ppt, tile_grid,
                                 tile_smem, tile_dbuf, tcs, tcl, s));

@@ -689,9 +689,11 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
                 }
             }
             // stop decisions.  The float32 gap of the large chain-like problems
-            // carries noise near 1e-5 (sums over thousands of table rows), so it
-            // only nominates points; the double-float32 re-check decides, at most
-            // once every 4 gap checks per point.
+            // carries noise near 1e-5 (K^T y is accumulated over thousands of
+            // table rows in float32), so it only nominates points; the
+            // double-float32 re-check (which reads the whole table) decides: at
+            // most once every 8 gap checks for a float32 gap within 1.5 tol, once
+            // every 32 checks within 4 tol.
             int cand = 0;
             if (check) {
                 const float quad = qs + 1.f;
@@ -703,7 +705,8 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
                     iters[pt] = cnt - 1;
                     status[pt] = HOPF_NONFINITE;
                     cand = 2;
-                } else if (gp <= 4.f * (float)prm.tol_gap && cnt - last_check >= 4 * prm.gap_every) {
+                } else if ((gp <= 1.5f * (float)prm.tol_gap && cnt - last_check >= 8 * prm.gap_every) ||
+                           (gp <= 4.f * (float)prm.tol_gap && cnt - last_check >= 32 * prm.gap_every)) {
                     cand = 1;
                     last_check = cnt;
                 } else if (cnt > prm.max_iter) {
@@ -717,43 +720,62 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
             }
             s_flag[tid] = cand;
             slots_sync();
-            // re-check of the nominated points, one slot at a time (whole slot group)
+            // re-check of the nominated points, one slot at a time (whole slot
+            // group), reading the float32 hi/lo split of the float64 table once
+            // per product.  The ring stages are idle here (this iteration's
+            // contractions are complete, the next one's copies wait for the
+            // iteration barrier): the point's pbar, x0 and y are gathered there,
+            // and the row products z_R = K_R pbar kept there in float64.
+            float *stage_f = reinterpret_cast<float *>(tsm);
+            float *pb_c = stage_f, *x_c = stage_f + n1, *y_c = stage_f + 2 * n1;
+            double *z_c = reinterpret_cast<double *>(stage_f + ((2 * n1 + rows + 1) & ~1LL));
             for (int s = 0; s < TC_PTS; ++s) {
                 if (s_flag[s] != 1) continue;                           // uniform (shared memory)
                 const float *pb_s = pbs + (long long)par * TC_PTS * n1 + s;   // element j at [j * TC_PTS]
-                const float *y_s = ys + s;
-                const float *x_s = xs + s;
-                // H = sum_i w_i |K_i pbar|_*: warp per node, lanes over the state
-                const int lane = tid & 31;
+                for (int j = tid; j < n1; j += TC_PTS) {
+                    pb_c[j] = j < n ? pb_s[j * TC_PTS] : 0.f;
+                    x_c[j] = j < n ? xs[j * TC_PTS + s] : 0.f;
+                }
+                for (long long R = tid; R < rows; R += TC_PTS) y_c[R] = ys[R * TC_PTS + s] * (1.f - 4e-7f);
+                // (y shrunk by 4e-7 so that float32 rounding cannot leave w_i U)
+                slots_sync();
+                // z_R = K_R pbar in double-float32, one thread per table row
+                for (long long R = tid; R < rows; R += TC_PTS) {
+                    DF a = {0.f, 0.f};
+                    const float4 *kh4 = reinterpret_cast<const float4 *>(im.Kh + R * n1);
+                    const float4 *kl4 = reinterpret_cast<const float4 *>(im.Kl + R * n1);
+#pragma unroll 4
+                    for (int q = 0; q < n1 / 4; ++q) {
+                        const float4 h = kh4[q], l = kl4[q];
+                        a = df_fma(a, h.x, l.x, pb_c[4 * q]);
+                        a = df_fma(a, h.y, l.y, pb_c[4 * q + 1]);
+                        a = df_fma(a, h.z, l.z, pb_c[4 * q + 2]);
+                        a = df_fma(a, h.w, l.w, pb_c[4 * q + 3]);
+                    }
+                    z_c[R] = (double)a.hi + (double)a.lo;
+                }
+                slots_sync();
+                // H = sum_i w_i |K_i pbar|_*
                 double hp = 0.0;
-                for (int i = warp; i < N; i += 4) {
+                for (int i = tid; i < N; i += TC_PTS) {
                     const long long R = (long long)(i / g.npb) * TC_NB + (i % g.npb) * g.mp;
                     double nt = 0.0;
-                    for (int c = 0; c < m; ++c) {
-                        DF a = {0.f, 0.f};
-                        const float *kh = im.Kh + (R + c) * n1, *kl = im.Kl + (R + c) * n1;
-                        for (int j = lane; j < n; j += 32) a = df_fma(a, kh[j], kl[j], pb_s[j * TC_PTS]);
-                        a = df_shfl_sum(a);
-                        const double zz = (double)a.hi + (double)a.lo;
-                        nt += ball ? zz * zz : fabs(zz);
-                    }
-                    if (lane == 0) hp += w64[i] * (ball ? sqrt(nt) : nt);
+                    for (int c = 0; c < m; ++c) nt += ball ? z_c[R + c] * z_c[R + c] : fabs(z_c[R + c]);
+                    hp += w64[i] * (ball ? sqrt(nt) : nt);
                 }
                 const double H64 = slots_sum(hp, red);
-                // u = x0 - K^T y, D = 1 - u^T V u, quad = pbar^T M pbar / 4 - <x0, pbar>
+                // u = x0 - K^T y (threads over state components, rows read
+                // coalesced), D = 1 - u^T V u, quad = pbar^T M pbar / 4 - <x0, pbar>
                 double dq = 0.0, qq = 0.0;
-                for (int j = warp; j < n; j += 4) {
+                for (int j = tid; j < n; j += TC_PTS) {
                     DF a = {0.f, 0.f};
-                    const float *kh = im.KTh + (long long)j * rows, *kl = im.KTl + (long long)j * rows;
-                    // y shrunk by 4e-7 so that float32 rounding cannot leave w_i U
-                    for (long long R = lane; R < rows; R += 32) a = df_fma(a, kh[R], kl[R], y_s[R * TC_PTS] * (1.f - 4e-7f));
-                    a = df_shfl_sum(a);
-                    if (lane == 0) {
-                        const double u = (double)x_s[j * TC_PTS] - ((double)a.hi + (double)a.lo);
-                        dq += u * u * Vd64[j];
-                        const double pb = (double)pb_s[j * TC_PTS];
-                        qq += pb * (0.25 * Md64[j] * pb - (double)x_s[j * TC_PTS]);
-                    }
+                    const float *kh = im.Kh + j, *kl = im.Kl + j;
+#pragma unroll 8
+                    for (int R = 0; R < (int)rows; ++R) a = df_fma(a, kh[(long long)R * n1], kl[(long long)R * n1], y_c[R]);
+                    const double u = (double)x_c[j] - ((double)a.hi + (double)a.lo);
+                    dq += u * u * Vd64[j];
+                    const double pb = (double)pb_c[j];
+                    qq += pb * (0.25 * Md64[j] * pb - (double)x_c[j]);
                 }
                 const double D64 = 1.0 - slots_sum(dq, red);
                 const double P64 = 1.0 + slots_sum(qq, red) + H64;
@@ -774,7 +796,9 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
             // finished slots take the next point; pbar images go to the bulk copies
             if (cand == 2) take_point();
             par ^= 1;
-            asm volatile("fence.proxy.async.global;" ::: "memory");
+            // generic writes (pbar images, gathered re-check operands in the ring)
+            // before the next iteration's bulk copies
+            asm volatile("fence.proxy.async;" ::: "memory");
         }
         // iteration boundary, all threads
         const int any = __syncthreads_or(slot_thread && pt >= 0);
@@ -806,7 +830,10 @@ static int tc_stages(const TcGeom &g, size_t smem_limit) {
 bool tc_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *grid) {
     if (n < 16 || n > 256 || m < 1 || m > 16 || N < 1 || P < 1) return false;
     const TcGeom g = tc_geom(n, m, N);
-    if (tc_stages(g, smem_limit) < 2) return false;
+    const int stages = tc_stages(g, smem_limit);
+    if (stages < 2) return false;
+    // the re-check gathers pbar, x0, y and keeps the row products (float64) in the ring
+    if ((2LL * g.n1 + 3LL * g.rows + 2) * 4 > (long long)stages * tc_stage_bytes(g)) return false;
     const int tiles = (P + TC_PTS - 1) / TC_PTS;
     *grid = tiles < sms ? tiles : sms;
     return true;
