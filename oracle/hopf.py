@@ -248,7 +248,10 @@ def relative_gap(Pv, Dv):
 
 
 # ---------------------------------------------------------------------- PDHG
-def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel=False):
+ADAPT_ALPHA0, ADAPT_ETA, ADAPT_DELTA = 0.5, 0.95, 1.5
+
+
+def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel=False, adaptive=False):
     """Chambolle-Pock iteration of Eq. 15 for every point in x0 (P, n).
 
       y <- prox_{sigma F*}(y + sigma K pbar)   (Eq. 23: projection onto w_i U per node)
@@ -265,6 +268,15 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel
     theta = 1/sqrt(1 + 2 gamma tau), tau <- theta tau, sigma <- sigma/theta and
     pbar = p_new + theta (p_new - p).  The prox of G is then (I + tau M/2)^-1
     at the current tau, evaluated by a fresh linear solve.
+
+    adaptive=True balances the two residuals that §III.B uses as its
+    stopping rule (after Goldstein et al., the adaptive PDHG cited there),
+      r_p = (p^k - p^{k-1})/tau - K^T (y^k - y^{k-1}),
+      r_d = (y^k - y^{k-1})/sigma - K (p^k - p^{k-1}):
+    after a step, if |r_p| > Delta |r_d| then tau <- tau/(1 - a),
+    sigma <- sigma (1 - a), a <- eta a; if |r_p| < |r_d|/Delta the reverse;
+    tau sigma stays 1/|K|^2 (a0 = 0.5, eta = 0.95, Delta = 1.5; no
+    backtracking).  theta stays 1; the prox of G is taken at the current tau.
     Returns dict(phi=-P, p, y, P, D, gap, iters, status)."""
     x0 = np.atleast_2d(np.asarray(x0, dtype=np.float64))
     P_, n = x0.shape
@@ -282,6 +294,8 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel
     active = np.arange(P_)
     tau_k = np.full(P_, float(tau))
     sig_k = np.array(sigma, dtype=np.float64)
+    alpha_k = np.full(P_, ADAPT_ALPHA0)
+    eye = np.eye(n)
     if accel:
         Mb = pb["M"] if pb["M"].shape[0] == P_ else np.broadcast_to(pb["M"], (P_,) + pb["M"].shape[1:])
         gamma = 0.5 * np.linalg.eigvalsh(Mb)[:, 0]
@@ -301,13 +315,31 @@ def pdhg(prob, x0, tol=1e-8, max_iter=200000, p0=None, y0=None, stop=None, accel
         ynew = project_scaled(kind, v, np.broadcast_to(wa, v.shape[:-1]))
         # primal step: prox of G (Eq. 37)
         rhs = p[active] - ta[:, None] * _KTy(Ka, ynew) + ta[:, None] * x0[active]
-        if accel:
+        if accel or adaptive:
             A_ = eye + 0.5 * ta[:, None, None] * np.broadcast_to(sub(pb["M"], active), (active.size, n, n))
+        if accel:
             pnew = np.linalg.solve(A_, rhs[..., None])[..., 0]
             th = 1.0 / np.sqrt(1.0 + 2.0 * gamma[active] * ta)
             tau_k[active] = th * ta
             sig_k[active] = sa / th
             pbar[active] = pnew + th[:, None] * (pnew - p[active])
+        elif adaptive:
+            pnew = np.linalg.solve(A_, rhs[..., None])[..., 0]
+            pbar[active] = 2.0 * pnew - p[active]
+            # residuals of §III.B at the step just taken, then the balance
+            dp = pnew - p[active]
+            dy = ynew - y[active]
+            r_p = dp / ta[:, None] - _KTy(Ka, dy)
+            r_d = dy / sa[:, None, None] - _Kp(Ka, dp)
+            npr = np.linalg.norm(r_p, axis=-1)
+            ndr = np.linalg.norm(r_d.reshape(active.size, -1), axis=-1)
+            al = alpha_k[active]
+            up = npr > ADAPT_DELTA * ndr
+            dn = ADAPT_DELTA * npr < ndr
+            fac = np.where(up, 1.0 / (1.0 - al), np.where(dn, 1.0 - al, 1.0))
+            tau_k[active] = ta * fac
+            sig_k[active] = sa / fac
+            alpha_k[active] = np.where(up | dn, ADAPT_ETA * al, al)
         else:
             pnew = np.einsum("...ij,...j->...i", Sa, rhs)
             pbar[active] = 2.0 * pnew - p[active]
@@ -356,7 +388,7 @@ def solve_in_variables(probs, x, p0=None, **kw):
 
 
 def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_scale=1.0, accel=False,
-          variables="initial"):
+          variables="initial", adaptive=False):
     """phi_N(x, T): the generalized Hopf formula with the N-node quadrature
     (Eq. 18) for every row of x at one horizon T.  At T = 0 the value is the
     terminal cost itself (Eq. 4 initial condition) and p* = grad J_x.
@@ -372,8 +404,8 @@ def value(sysd, x, T, N, rule, tau, tol=1e-8, max_iter=200000, p0=None, sigma_sc
                     P=-terminal_cost(sysd, x), D=-terminal_cost(sysd, x))
     prob = setup(sysd, T, N, rule, tau, sigma_scale, variables)
     if variables == "initial":
-        return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0, accel=accel)
-    return solve_in_variables(prob, x, p0=p0, tol=tol, max_iter=max_iter, accel=accel)
+        return pdhg(prob, x, tol=tol, max_iter=max_iter, p0=p0, accel=accel, adaptive=adaptive)
+    return solve_in_variables(prob, x, p0=p0, tol=tol, max_iter=max_iter, accel=accel, adaptive=adaptive)
 
 
 # ---------------------------------------------------------------- time-to-reach

@@ -359,3 +359,23 @@ def test_identical_stacked_copies_reduce_to_the_base_problem():
         a = oh.value(w["system"], w["x"], T, 40, oh.LEFT_RIEMANN, 0.5, tol=1e-11)["phi"]
         b = oh.value(base, w["mu"], T, 40, oh.LEFT_RIEMANN, 0.5, tol=1e-11)["phi"]
         assert np.allclose(a, b, rtol=1e-8), (a, b)
+
+
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_adaptive_steps_reach_the_independent_value(variables):
+    # Residual-balanced steps (§III.B residuals, Goldstein et al.'s adaptive
+    # PDHG) change tau and sigma as they go but converge to the same
+    # discretised value; pinned against the projected-gradient solver, ball
+    # and box control
+    sysd = wl.random_system(11, 4, 2)
+    x = wl.normal_points(12, 3, 4, 1.0)
+    res = oh.value(sysd, x, 0.8, 24, oh.LEFT_RIEMANN, tau=0.2, tol=1e-12, adaptive=True, variables=variables)
+    assert np.all(res["status"] == oh.OK)
+    for k in range(3):
+        ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x[k], 0.8, 24, "ball")
+        assert abs(res["phi"][k] - ref) <= 1e-8 * max(1.0, abs(ref))
+    sysd = wl.double_integrator(0.1)
+    x0 = np.array([0.6, -0.3])
+    r1 = oh.value(sysd, x0, 1.0, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, adaptive=True, variables=variables)
+    ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 32, "box", trapezoid=True)
+    assert abs(r1["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
