@@ -151,6 +151,14 @@ typedef struct {
                            per point (0 = 256).  A point still open at the cap
                            returns T_star = the top of its bracket and the status
                            HOPF_MAXITER.                                          */
+    int adaptive;       /* 1: step sizes balanced on the two residuals §III.B uses
+                           for its stopping rule (the adaptive PDHG of Goldstein
+                           et al. cited there): after each step, if
+                           |r_p| > 1.5 |r_d| then tau /= (1 - a), sigma *= (1 - a),
+                           if 1.5 |r_p| < |r_d| the reverse, then a *= 0.95
+                           (a starts at 0.5; tau sigma stays 1/|K|^2).  Runs on
+                           the general warp-per-point kernel; not with accel,
+                           the warm start or the stacked solve.                  */
 } hopf_opts;
 
 #define HOPF_KERNEL_AUTO 0
@@ -381,7 +389,7 @@ int hopf_tc_selftest(int N, int K, const float *A, const float *B, float *D, int
  *   - n <= HOPF_NOALLOC_MAX_N, m <= 16;
  *   - opts->variables must be HOPF_VARS_INITIAL;
  *   - the scratch the call needs must fit the array, about
- *     8 (n_tables (N m n + N + 6 n^2 + n) + 9 n^2) + P N m sizeof(element)
+ *     8 (n_tables (N m n + N + 7 n^2 + n) + 9 n^2) + P N m sizeof(element)
  *     bytes with n_tables = 1 (t_stride 0) or P (t_stride 1); otherwise the
  *     call returns HOPF_ESCRATCH and does nothing.
  *   Validation failures return the codes of hopf_value; hopf_last_error() is

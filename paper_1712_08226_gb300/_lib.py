@@ -20,7 +20,8 @@ class HopfOpts(ctypes.Structure):
                 ("precision", c_int), ("host_io", c_int), ("tau", c_double), ("sigma_scale", c_double),
                 ("tol_gap", c_double), ("t_max", c_double), ("tol_T", c_double), ("profile", c_int),
                 ("accel", c_int), ("park_iters", c_int), ("newton", c_int),
-                ("kernel", c_int), ("variables", c_int), ("max_steps", c_int)]
+                ("kernel", c_int), ("variables", c_int), ("max_steps", c_int),
+                ("adaptive", c_int)]
 
 
 class HopfMlp(ctypes.Structure):

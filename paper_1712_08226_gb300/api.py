@@ -70,12 +70,14 @@ class Options:
     kernel: int = 0          # 0 auto, 1 force one warp per point
     variables: int = VARS_INITIAL   # VARS_TERMINAL: iterate in q, p = e^{T A^T} q
     max_steps: int = 0       # time-to-reach: cap on candidate horizons per point (0 = 256)
+    adaptive: bool = False   # residual-balanced step sizes (general kernel)
 
     def c_struct(self, host_io):
         return _lib.HopfOpts(self.rule, self.N, self.max_iter, self.gap_every, self.precision, int(host_io),
                              self.tau, self.sigma_scale, self.tol_gap, self.t_max, self.tol_T,
                              int(self.profile), int(self.accel), int(self.park_iters),
-                             int(self.newton), int(self.kernel), int(self.variables), int(self.max_steps))
+                             int(self.newton), int(self.kernel), int(self.variables), int(self.max_steps),
+                             int(self.adaptive))
 
 
 def _is_torch(a):

@@ -320,6 +320,8 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
             return fail(HOPF_EINVAL, "kernel must be one of HOPF_KERNEL_AUTO, _GENERIC, _TENSOR, _TILE");
         if (o->variables != HOPF_VARS_INITIAL && o->variables != HOPF_VARS_TERMINAL)
             return fail(HOPF_EINVAL, "variables must be HOPF_VARS_INITIAL or HOPF_VARS_TERMINAL");
+        if (o->adaptive != 0 && o->adaptive != 1) return fail(HOPF_EINVAL, "adaptive must be 0 or 1");
+        if (o->adaptive && o->accel) return fail(HOPF_EINVAL, "adaptive and accel exclude each other");
     }
     return HOPF_SUCCESS;
 }
@@ -487,6 +489,7 @@ void fill_params(SolveParams &prm, const hopf_problem *pr, const hopf_opts *o, i
     prm.sign_mode = 0;
     prm.inst_stride = 0;
     prm.accel = o->accel;
+    prm.adaptive = o->adaptive;
     prm.tau = o->tau;
     prm.tol_gap = o->tol_gap;
     prm.sign_floor = o->precision == HOPF_FP64 ? 1e-13 : 1e-6;
@@ -504,8 +507,8 @@ int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *
                   const int *active, int n_inst, double *inst64, float *inst32, double *scratch, int grid,
                   cudaStream_t s) {
     CU(launch_build_instances_opt(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
-                                  pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch, o->accel,
-                                  o->variables == HOPF_VARS_TERMINAL));
+                                  pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch,
+                                  o->accel || o->adaptive, o->variables == HOPF_VARS_TERMINAL));
     return HOPF_SUCCESS;
 }
 
@@ -543,17 +546,17 @@ int value_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_
     if (rc) return rc;
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     SmallPlan sp, sp32;
-    if (fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO) {
+    if (fp32 && t_stride == 0 && o->kernel == HOPF_KERNEL_AUTO && !o->adaptive) {
         sp = plan_small(dev, n, m, N, P);
         sp32 = plan_small(dev, n, m, N, P, 32);
         sp32.grid = dev.sms;
     }
     // large states, one shared table: the tensor-core kernel or the tiled kernel
     int tc_grid = 0;
-    const bool tcore = !sp.ok && want_tc(pr, o, t_stride, P, dev, &tc_grid);
+    const bool tcore = !sp.ok && !o->adaptive && want_tc(pr, o, t_stride, P, dev, &tc_grid);
     int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
     size_t tile_smem = 0;
-    const bool tile = fp32 && t_stride == 0 && !tcore && !sp.ok &&
+    const bool tile = fp32 && t_stride == 0 && !tcore && !sp.ok && !o->adaptive &&
                       (o->kernel == HOPF_KERNEL_AUTO || o->kernel == HOPF_KERNEL_TILE) &&
                       tile_plan(n, m, N, P, dev.sms, dev.smem_optin - 2048, &tile_ppt, &tile_grid, &tile_smem,
                                 &tile_dbuf);
@@ -685,6 +688,7 @@ int stacked_impl(const hopf_stacked *sp, const hopf_opts *o, int P, const void *
     const hopf_problem *pr = &sp->base;
     const int nb = pr->n, m = pr->m, N = o->N, k = sp->copies;
     if (o->variables != HOPF_VARS_INITIAL) return fail(HOPF_EINVAL, "stacked solve: variables must be HOPF_VARS_INITIAL");
+    if (o->adaptive) return fail(HOPF_EINVAL, "stacked solve: adaptive steps are not supported");
     const bool fp32 = o->precision == HOPF_FP32;
     const int nT = t_stride ? P : 1;
     const int n_inst = nT * k;
@@ -1380,6 +1384,7 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
     if (rc) return rc;
     rc = check_mlp(net);
     if (rc) return rc;
+    if (opts->adaptive) return fail(HOPF_EINVAL, "warm start: adaptive steps are not supported");
     if (opts->precision != HOPF_FP32) return fail(HOPF_EINVAL, "warm start: FP32 only");
     if (net->n_in != prob->n || net->n_out != prob->n) return fail(HOPF_EINVAL, "network must map R^n to R^n");
     if (P < 0 || (t_stride != 0 && t_stride != 1) || max_iter_warm < 0) return fail(HOPF_EINVAL, "bad P/t_stride");

@@ -9,6 +9,8 @@
 //   S    [n][n]     (I + tau M / 2)^-1                          (Eq. 37)
 //   U    [n][n]     eigenvectors of M (M = U diag(lam) U^T), for the
 //   lam  [n]        accelerated iteration whose step tau changes every step
+//   G    [n][n]     Gram matrix sum_i K_i^T K_i (|K|^2 is its largest
+//                   eigenvalue; |K d|^2 = d^T G d for the adaptive steps)
 //   E    [n][n]     e^{TA}: maps the query point to the terminal-time variable
 //   Ei   [n][n]     e^{-TA}  (both the identity for the paper's variable)
 //   sc   [8]        sigma, T, |K|^2, flag (1 = T == 0), gamma = lambda_min(M)/2
@@ -25,7 +27,7 @@ namespace hopf {
 
 struct InstanceLayout {
     // element offsets (in elements of the instance's type) inside one instance
-    long long K, w, M, V, S, U, lam, E, Ei, sc, stride;
+    long long K, w, M, V, S, U, lam, G, E, Ei, sc, stride;
     __host__ __device__ static InstanceLayout make(int n, int m, int N) {
         InstanceLayout L;
         long long o = 0;
@@ -37,6 +39,7 @@ struct InstanceLayout {
         L.S = o;  o = al(o + (long long)n * n);
         L.U = o;  o = al(o + (long long)n * n);
         L.lam = o; o = al(o + n);
+        L.G = o;  o = al(o + (long long)n * n);
         L.E = o;  o = al(o + (long long)n * n);
         L.Ei = o; o = al(o + (long long)n * n);
         L.sc = o; o = al(o + 8);
@@ -54,6 +57,7 @@ struct SolveParams {
     int sign_mode;     // time-to-reach: stop once the sign of phi is certified
     int inst_stride;   // 0: one shared instance, 1: instance k for point k
     int accel;         // Chambolle-Pock accelerated variant (strongly convex G)
+    int adaptive;      // residual-balanced step sizes (general kernel)
     const int *list;        // optional: solve only the points list[0 .. *list_count)
     const int *list_count;  // device count for `list`
     // multi-phase solve of the small-state kernels: a phase parks every point

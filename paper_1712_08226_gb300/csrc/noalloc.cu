@@ -129,6 +129,7 @@ int validate(const hopf_problem *pr, const hopf_opts *o) {
     if (!(o->tol_gap >= 0.0)) return HOPF_EINVAL;
     if (o->accel != 0 && o->accel != 1) return HOPF_EINVAL;
     if (o->variables != HOPF_VARS_INITIAL) return HOPF_EINVAL;   // the paper's variable only
+    if (o->adaptive) return HOPF_EINVAL;
     return HOPF_SUCCESS;
 }
 

@@ -21,6 +21,15 @@
 // Lanes of a warp split the nodes in the dual step and the state components
 // in the K^T y, S and quadratic-form products.  The dual variable y lives in
 // a global scratch array (N m values per point).
+//
+// Adaptive steps (prm.adaptive): after a step the residuals of §III.B,
+//   r_p = (p^k - p^{k-1})/tau - K^T (y^k - y^{k-1}),
+//   r_d = (y^k - y^{k-1})/sigma - K (p^k - p^{k-1}),
+// are measured (|r_d|^2 = |dy|^2/sigma^2 - 2 <K^T dy, dp>/sigma + dp^T G dp
+// with the Gram matrix G = K^T K of the table) and balanced (Goldstein et
+// al.): tau /= (1 - a), sigma *= (1 - a) when |r_p| > 1.5 |r_d|, the reverse
+// when 1.5 |r_p| < |r_d|, a *= 0.95 after a change; the prox of G is then
+// taken at the current tau through M = U diag(lam) U^T.
 #include "common.cuh"
 
 namespace hopf {
@@ -53,8 +62,9 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     }
     if (active && !active[k]) return;
     extern __shared__ unsigned char smem_raw[];
-    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 6 * n;
+    R *sm = reinterpret_cast<R *>(smem_raw) + (size_t)warp * 7 * n;
     R *p = sm, *pb = sm + n, *qv = sm + 2 * n, *acc = sm + 3 * n, *x0 = sm + 4 * n, *vt = sm + 5 * n;
+    R *accp = sm + 6 * n;                                      // K^T y of the previous step (adaptive)
 
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     const R *I = inst_base + (prm.inst_stride ? (long long)k * L.stride : 0LL);
@@ -63,7 +73,8 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     const R gamma = sc[SC_GAMMA];
     const bool zero = sc[SC_ZERO] != R(0);
     R tau = (R)prm.tau;
-    const R *U = I + L.U, *lam = I + L.lam;
+    const R *U = I + L.U, *lam = I + L.lam, *G = I + L.G;
+    R alpha = R(0.5);
     R *y = y_scratch + (long long)k * N * m;
     const bool ball = prm.ctrl_kind == HOPF_BALL;
 
@@ -119,6 +130,15 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
         }
     }
     __syncwarp();
+    if (prm.adaptive) {
+        for (int j = lane; j < n; j += 32) {
+            R s = 0;
+            for (int i = 0; i < N; ++i)
+                for (int c = 0; c < m; ++c) s = fma(K[((long long)i * m + c) * n + j], y[(long long)i * m + c], s);
+            accp[j] = s;
+        }
+        __syncwarp();
+    }
 
     const int g = prm.gap_every;
     auto is_check = [&](int it) { return it >= 2 && (it % g == 0 || it > prm.max_iter); };
@@ -129,7 +149,7 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
         const bool check = is_check(it);
         for (int j = lane; j < n; j += 32) qv[j] = sigma * pb[j];
         __syncwarp();
-        R hs = 0;
+        R hs = 0, dy2 = 0;
         for (int i = lane; i < N; i += 32) {
             R t[GEN_MMAX];
             const R *Ki = K + (long long)i * m * n;
@@ -147,9 +167,17 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
             if (check) hs = fma(wi, ball ? sqrt(nt) : nt, hs);
             if (ball) {
                 R scale = (nu > wi * wi) ? wi / sqrt(nu) : R(1);
-                for (int c = 0; c < m; ++c) yi[c] = t[c] * scale;
+                for (int c = 0; c < m; ++c) {
+                    const R yn = t[c] * scale;
+                    if (prm.adaptive) dy2 = fma(yn - yi[c], yn - yi[c], dy2);
+                    yi[c] = yn;
+                }
             } else {
-                for (int c = 0; c < m; ++c) yi[c] = fmin(fmax(t[c], -wi), wi);
+                for (int c = 0; c < m; ++c) {
+                    const R yn = fmin(fmax(t[c], -wi), wi);
+                    if (prm.adaptive) dy2 = fma(yn - yi[c], yn - yi[c], dy2);
+                    yi[c] = yn;
+                }
             }
         }
         if (check) {
@@ -202,6 +230,48 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
             }
             tau *= th;
             sigma /= th;
+        } else if (prm.adaptive) {
+            // prox of G at the current tau, then the residual balance
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(U[l * n + j], vt[l], s);
+                qv[j] = s / fma(R(0.5) * tau, lam[j], R(1));
+            }
+            __syncwarp();
+            for (int j = lane; j < n; j += 32) {
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(U[j * n + l], qv[l], s);
+                vt[j] = s - p[j];                  // dp (vt is free until the next step)
+                pb[j] = R(2) * s - p[j];
+                p[j] = s;
+            }
+            __syncwarp();
+            R rp2 = 0, cross = 0, qg = 0;
+            for (int j = lane; j < n; j += 32) {
+                const R da = acc[j] - accp[j];
+                const R r = vt[j] / tau - da;
+                rp2 = fma(r, r, rp2);
+                cross = fma(da, vt[j], cross);
+                R s = 0;
+                for (int l = 0; l < n; ++l) s = fma(G[j * n + l], vt[l], s);
+                qg = fma(vt[j], s, qg);
+                accp[j] = acc[j];
+            }
+            rp2 = warp_sum(rp2);
+            cross = warp_sum(cross);
+            qg = warp_sum(qg);
+            const R dyy = warp_sum(dy2);
+            const R rd2 = fmax(dyy / (sigma * sigma) - R(2) * cross / sigma + qg, R(0));
+            const R npr = sqrt(rp2), ndr = sqrt(rd2);
+            if (npr > R(1.5) * ndr) {
+                tau /= (R(1) - alpha);
+                sigma *= (R(1) - alpha);
+                alpha *= R(0.95);
+            } else if (R(1.5) * npr < ndr) {
+                tau *= (R(1) - alpha);
+                sigma /= (R(1) - alpha);
+                alpha *= R(0.95);
+            }
         } else {
             for (int j = lane; j < n; j += 32) {
                 R s = 0;
@@ -242,7 +312,7 @@ cudaError_t launch_pdhg_generic(const R *inst, const SolveParams &prm, const R *
     constexpr int warps = 4;
     const int threads = warps * 32;
     const int grid = (prm.P + warps - 1) / warps;
-    const size_t smem = (size_t)warps * 6 * prm.n * sizeof(R);
+    const size_t smem = (size_t)warps * 7 * prm.n * sizeof(R);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(pdhg_generic_kernel<R>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -126,6 +126,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
             }
         }
         __syncthreads();
+        cta::copy(o + L.G, C, n * n);
         // |K|^2 = largest eigenvalue of the Gram matrix: Jacobi for small n
         // (a few hundred block barriers), the power method otherwise
         double L2;
