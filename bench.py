@@ -599,7 +599,8 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
 def run_chain_ttr(args):
     """Secondary line: minimum time to reach for the 100-mass chain (§IV),
     bisection or (--newton) the Newton hybrid on [0, --t-max] with per-point
-    node tables (N = 512, float32 solves to gap 1e-5, tol_T 1e-5)."""
+    node tables (N = 512, float32 solves to gap 1e-5, tol_T 1e-5), in
+    terminal-time variables (tau 0.1) unless --paper-variables."""
     rank, world, local = rank_env()
     import torch
     torch.cuda.set_device(local)
@@ -608,10 +609,12 @@ def run_chain_ttr(args):
     build.build()
     H._lib.load()
     P = args.points if args.points != POINTS else 64
-    n, N = 200, 512
+    n, m, N = 200, 10, 512
     sysd = H.System.from_dict(wl.spring_chain())
     x = torch.tensor(wl.normal_points(3 + 1000 * rank, P, n, 1.0), dtype=torch.float32, device="cuda")
-    o = H.Options(N=N, tau=0.5, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5, max_iter=args.max_iter, newton=args.newton)
+    variables = H.VARS_INITIAL if args.paper_variables else H.VARS_TERMINAL
+    o = H.Options(N=N, tau=0.5 if args.paper_variables else 0.1, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5,
+                  max_iter=args.max_iter, newton=args.newton, variables=variables)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         H.time_to_reach(sysd, x, o)
@@ -636,16 +639,18 @@ def run_chain_ttr(args):
         "metric": "time-to-reach solves/sec (chain workload)", "value": ok / args.steps / t, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax{args.t_max:g}_N512_{P}pts", "n": n, "m": 10, "N": N,
+        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax{args.t_max:g}_N512_{P}pts", "n": n, "m": m, "N": N,
                    "t_max": args.t_max, "tol_gap": TOL, "tol_T": 1e-5, "points": P,
+                   "variables": "paper's p" if args.paper_variables else "terminal-time q",
                    "search": "newton hybrid" if args.newton else "certified bisection", "rounds": steps,
                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(r["status"].cpu().numpy(),
                                                                             return_counts=True))},
                    "T_mean": float(Tv.mean()), "T_max": float(Tv.max()),
                    "tables": "one float64 table per point and candidate horizon"},
         "roofline": {"bound": "hbm", "kernel": "pdhg_generic_kernel<float> (per-point tables)", "achieved": None,
-                     "peak": 6795.8, "unit": "GB/s", "frac": None, "traffic": None,
-                     "note": "each point reads its own 4 MB float32 table twice per iteration"},
+                     "peak": measured_peaks()[0]["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None,
+                     "note": "each point reads its own 4 MB float32 table twice per iteration; the step also "
+                             "builds one float64 table per point and candidate"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
