@@ -10,7 +10,8 @@ Everything is plain float64 numpy, written to be read side by side with the
 paper (Kirchner, Hewer, Darbon, Osher, "A Primal-Dual Method for Optimal
 Control and Trajectory Generation in High-Dimensional Systems"):
 
-  * quadrature nodes and weights ............ §III.A, Eq. 17 (+ trapezoid rule)
+  * quadrature nodes and weights ............ §III.A, Eq. 17 (+ trapezoid rule,
+                                              + the fixed-step left sum FixedStep)
   * node matrices K_i ....................... §III.A, Eq. 16 and Eq. 20
   * quadratic terminal cost and its conjugate §VI.A, Eq. 34 - Eq. 37
   * primal-dual iteration ................... §III, Eq. 15 with Eq. 22, Eq. 23, Eq. 37
@@ -46,6 +47,33 @@ OK, MAXITER, NONFINITE, UNREACHABLE, AMBIGUOUS_SIGN = 0, 1, 2, 3, 4
 
 
 # ----------------------------------------------------------------- quadrature
+class FixedStep:
+    """Left Riemann sum with a step that does not depend on T: dt = t_max / N.
+
+    §III.A takes N equal steps of T / N and allows other quadratures.  Here
+    the step is fixed: the nodes are t_i = i dt for every i >= 0 with
+    t_i < T, each weighted dt, except the last, weighted T - t_last.  This is
+    the left Riemann sum of the partition {0, dt, 2 dt, ..., t_last, T}; at
+    T = k dt it is Eq. 17 with k nodes.  In terminal-time variables the node
+    matrices (-e^{t_i A} B Q)^T do not depend on T, so one table on
+    [0, t_max] serves every horizon (the nodes of horizon T are a prefix of
+    it).  N is the node count of that table: at most N nodes, T <= t_max."""
+
+    def __init__(self, t_max, N):
+        self.t_max = float(t_max)
+        self.N = int(N)
+        self.dt = self.t_max / self.N
+
+    def count(self, T):
+        """Number of nodes of horizon T > 0: the i >= 0 with i dt < T."""
+        if not (0.0 < T <= self.t_max):
+            raise ValueError("the fixed-step rule needs 0 < T <= t_max")
+        return min(max(int(np.ceil(T / self.dt)), 1), self.N)
+
+    def __eq__(self, other):
+        return isinstance(other, FixedStep) and (other.t_max, other.N) == (self.t_max, self.N)
+
+
 def nodes(T, N, rule):
     """Quadrature in Hopf time on [0, T].
 
@@ -54,8 +82,15 @@ def nodes(T, N, rule):
     both ends, t_i = i T/(N-1), weights T/(N-1) with the two end weights halved.
     Composite Simpson rule (also named there): N odd samples including both
     ends, t_i = i h with h = T/(N-1), weights h/3 (1, 4, 2, 4, ..., 2, 4, 1).
+    FixedStep(t_max, N): t_i = i dt (dt = t_max/N) while t_i < T, weights dt,
+    the last one T - t_last (len(t) <= N nodes).
     Returns (t, w)."""
-    if rule == LEFT_RIEMANN:
+    if isinstance(rule, FixedStep):
+        k = rule.count(T)
+        t = np.arange(k, dtype=np.float64) * rule.dt
+        w = np.full(k, rule.dt)
+        w[-1] = T - (k - 1) * rule.dt
+    elif rule == LEFT_RIEMANN:
         t = np.arange(N, dtype=np.float64) * (T / N)
         w = np.full(N, T / N)
     elif rule == TRAPEZOID:
@@ -123,8 +158,8 @@ def node_matrices(sysd, T, N, rule):
     A, B = sysd["A"], sysd["B"]
     Q = control_scaling(sysd)
     t, _ = nodes(T, N, rule)
-    K = np.empty((N, B.shape[1], A.shape[0]))
-    for i in range(N):
+    K = np.empty((t.size, B.shape[1], A.shape[0]))
+    for i in range(t.size):
         K[i] = -(expm(-(T - t[i]) * A) @ B @ Q).T
     return K
 
@@ -136,8 +171,8 @@ def node_matrices_terminal(sysd, T, N, rule):
     A, B = sysd["A"], sysd["B"]
     Q = control_scaling(sysd)
     t, _ = nodes(T, N, rule)
-    K = np.empty((N, B.shape[1], A.shape[0]))
-    for i in range(N):
+    K = np.empty((t.size, B.shape[1], A.shape[0]))
+    for i in range(t.size):
         K[i] = -(expm(t[i] * A) @ B @ Q).T
     return K
 
@@ -194,9 +229,19 @@ def setup(sysd, T, N, rule, tau, sigma_scale=1.0, variables="initial"):
 
 
 def _batched(prob_list):
-    """Stack per-point problems (same n, m, N) along a leading point axis."""
+    """Stack per-point problems (same n, m) along a leading point axis.  Node
+    counts that differ (the fixed-step rule) are padded with zero rows of K
+    and zero weights: such a node adds 0 to every sum, its dual variable is
+    held at 0 by the projection onto 0 U, and |K| is unchanged."""
+    Nmax = max(p["K"].shape[0] for p in prob_list)
+
+    def pad(p, k):
+        a = p[k]
+        if k not in ("K", "w") or a.shape[0] == Nmax:
+            return a
+        return np.concatenate([a, np.zeros((Nmax - a.shape[0],) + a.shape[1:])])
     keys = ("K", "w", "M", "V", "S")
-    out = {k: np.stack([p[k] for p in prob_list]) for k in keys}
+    out = {k: np.stack([pad(p, k) for p in prob_list]) for k in keys}
     out["sigma"] = np.array([p["sigma"] for p in prob_list])
     out["tau"] = prob_list[0]["tau"]
     out["kind"] = prob_list[0]["kind"]

@@ -28,10 +28,24 @@ def quad_nodes(T, N, trapezoid):
     return t, w
 
 
-def control_form(A, B, T, N, trapezoid):
-    """c = e^{TA} x0 map and G = [w_i e^{t_i A} B]_i (n x N m)."""
-    t, w = quad_nodes(T, N, trapezoid)
-    G = np.concatenate([w[i] * expm(t[i] * A) @ B for i in range(N)], axis=1)
+def fixed_step_nodes(T, dt):
+    """Left ends of the partition 0, dt, 2 dt, ... of [0, T], the last piece
+    running to T: nodes t_k = k dt while k dt < T, widths dt and T - t_last."""
+    t = []
+    k = 0
+    while k * dt < T:
+        t.append(k * dt)
+        k += 1
+    w = [dt] * len(t)
+    w[-1] = T - t[-1]
+    return np.array(t), np.array(w)
+
+
+def control_form(A, B, T, N, trapezoid, tw=None):
+    """c = e^{TA} x0 map and G = [w_i e^{t_i A} B]_i (n x N m); tw = (t, w)
+    gives the nodes explicitly."""
+    t, w = quad_nodes(T, N, trapezoid) if tw is None else tw
+    G = np.concatenate([w[i] * expm(t[i] * A) @ B for i in range(len(t))], axis=1)
     return expm(T * A), G
 
 
@@ -45,12 +59,12 @@ def _project(u, kind, m, bounds):
     return U.ravel()
 
 
-def fista_value(A, B, W, x0, T, N, kind, bound=1.0, trapezoid=False, iters=200000, tol=1e-15):
+def fista_value(A, B, W, x0, T, N, kind, bound=1.0, trapezoid=False, iters=200000, tol=1e-15, tw=None):
     """min over u_i in U of (e^{TA}x0 + G u)^T W^-1 (...) - 1 by FISTA with
     projection onto the product of control sets (ball radius `bound`, or box
     half-widths `bound` given as scalar or (m,) array)."""
     m = B.shape[1]
-    E, G = control_form(A, B, T, N, trapezoid)
+    E, G = control_form(A, B, T, N, trapezoid, tw)
     Wi = np.linalg.inv(W)
     c = E @ x0
     H = G.T @ Wi @ G

@@ -379,3 +379,68 @@ def test_adaptive_steps_reach_the_independent_value(variables):
     r1 = oh.value(sysd, x0, 1.0, 32, oh.TRAPEZOID, tau=2.0, tol=1e-12, adaptive=True, variables=variables)
     ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x0, 1.0, 32, "box", trapezoid=True)
     assert abs(r1["phi"][0] - ref) <= 1e-8 * max(1.0, abs(ref))
+
+
+# ------------------------------------------------ fixed-step quadrature rule
+def test_fixed_step_nodes_are_the_partition_and_reduce_to_eq17():
+    # The nodes of horizon T are the left ends of the partition {0, dt, ...,
+    # t_last, T} (walked independently here); at T = k dt they are Eq. 17 with
+    # k nodes; the weights always sum to T.
+    rule = oh.FixedStep(4.0, 64)
+    for T in (0.01, 0.0625, 0.3, 1.0, 1.23456, 3.99, 4.0):
+        t, w = oh.nodes(T, 64, rule)
+        tr, wr = ind.fixed_step_nodes(T, 4.0 / 64)
+        assert t.size == tr.size and np.allclose(t, tr, rtol=0, atol=1e-15) and np.allclose(w, wr, rtol=1e-12)
+        assert abs(w.sum() - T) <= 1e-14 * T and np.all(w > 0) and np.all(t < T)
+    for k in (1, 5, 17, 64):
+        t, w = oh.nodes(k * rule.dt, 64, rule)
+        tl, wl = oh.nodes(k * rule.dt, k, oh.LEFT_RIEMANN)
+        assert np.allclose(t, tl, rtol=1e-15, atol=0) and np.allclose(w, wl, rtol=1e-15)
+    with pytest.raises(ValueError):
+        oh.nodes(4.5, 64, rule)
+
+
+def test_fixed_step_single_integrator_time_to_reach_closed_form():
+    # A = 0: the value depends on the weights only through their sum, so the
+    # fixed-step rule is exact at every T, not only at multiples of the step:
+    # T* = max(|x| - r, 0) / rho.  A wrong last weight moves T* off it.
+    n, rho, r = 2, 1.0, 0.5
+    sysd = wl.single_integrator(n, oh.BALL, radius=rho, radius_target=r)
+    x = np.array([[1.5, 0.2], [0.1, 0.2], [-2.0, 2.5], [0.7, -0.45]])
+    for variables in ("initial", "terminal"):
+        res = oh.time_to_reach(sysd, x, 6.0, 8, oh.FixedStep(6.0, 8), tau=1.0, tol_T=1e-8,
+                               variables=variables)
+        exact = np.maximum(np.linalg.norm(x, axis=1) - r, 0.0) / rho
+        assert np.allclose(res["T"], exact, rtol=2e-7, atol=1e-9), (variables, res["T"], exact)
+
+
+@pytest.mark.parametrize("variables", ["initial", "terminal"])
+def test_fixed_step_value_equals_independent_projected_gradient(variables):
+    # phi with the fixed-step nodes against FISTA on the primal control form
+    # with the partition nodes built independently, at horizons between
+    # multiples of the step (a partial last node).
+    sysd = wl.random_system(11, 4, 2)
+    x = wl.normal_points(12, 2, 4, 1.0)
+    rule = oh.FixedStep(2.0, 40)
+    for T in (0.77, 1.313):
+        res = oh.value(sysd, x, T, 40, rule, tau=0.2, tol=1e-12, variables=variables)
+        for k in range(2):
+            ref, _ = ind.fista_value(sysd["A"], sysd["B"], sysd["W"], x[k], T, 0, "ball",
+                                     tw=ind.fixed_step_nodes(T, rule.dt))
+            assert abs(res["phi"][k] - ref) <= 1e-8 * max(1.0, abs(ref)), (T, k, res["phi"][k], ref)
+
+
+def test_fixed_step_di_time_to_reach_within_switching_curve_bound():
+    # The double integrator's time to reach a ball of radius r lies below the
+    # bang-bang time to the origin by at most the worst time from inside the
+    # ball; the fixed-step bisection lands there and agrees with the
+    # uniform-step rule to the quadrature error.
+    sysd = wl.double_integrator(0.1)
+    x = np.array([[1.0, 0.5], [-1.2, 0.3]])
+    rf = oh.time_to_reach(sysd, x, 8.0, 512, oh.FixedStep(8.0, 512), tau=2.0, tol_T=1e-8,
+                          variables="terminal")
+    ru = oh.time_to_reach(sysd, x, 8.0, 256, oh.LEFT_RIEMANN, tau=2.0, tol_T=1e-8, variables="terminal")
+    for k in range(2):
+        T0 = ind.di_min_time_to_origin(x[k])
+        assert 0.0 <= T0 - rf["T"][k] <= 0.1 + 2.0 * np.sqrt(0.1 + 0.005) + 1e-2
+    assert np.allclose(rf["T"], ru["T"], rtol=2e-3), (rf["T"], ru["T"])
