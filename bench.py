@@ -598,9 +598,12 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
 
 def run_chain_ttr(args):
     """Secondary line: minimum time to reach for the 100-mass chain (§IV),
-    bisection or (--newton) the Newton hybrid on [0, --t-max] with per-point
-    node tables (N = 512, float32 solves to gap 1e-5, tol_T 1e-5), in
-    terminal-time variables (tau 0.1) unless --paper-variables."""
+    bisection or (--newton) the Newton hybrid on [0, --t-max], float32 solves
+    to gap 1e-5, tol_T 1e-5, terminal-time variables (tau 0.1).  Default: the
+    fixed-step rule (one table of 2048 nodes on [0, 40], the paper's step
+    10/512) for all 4,096 chain points; --ttr-rule paper: Eq. 17 with N = 512
+    and one table per point and candidate (64 points; --paper-variables runs
+    it in the paper's variable)."""
     rank, world, local = rank_env()
     import torch
     torch.cuda.set_device(local)
@@ -608,12 +611,15 @@ def run_chain_ttr(args):
     from paper_1712_08226_gb300 import build
     build.build()
     H._lib.load()
-    P = args.points if args.points != POINTS else 64
-    n, m, N = 200, 10, 512
+    fixed = args.ttr_rule == "fixed"
+    P = args.points if args.points != POINTS else (4096 if fixed else 64)
+    n, m = 200, 10
+    N = int(round(2048 * args.t_max / 40.0)) if fixed else 512     # fixed step 40/2048 = 10/512
     sysd = H.System.from_dict(wl.spring_chain())
     x = torch.tensor(wl.normal_points(3 + 1000 * rank, P, n, 1.0), dtype=torch.float32, device="cuda")
-    variables = H.VARS_INITIAL if args.paper_variables else H.VARS_TERMINAL
-    o = H.Options(N=N, tau=0.5 if args.paper_variables else 0.1, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5,
+    variables = H.VARS_INITIAL if (args.paper_variables and not fixed) else H.VARS_TERMINAL
+    o = H.Options(rule=H.LEFT_FIXED if fixed else H.LEFT_RIEMANN, N=N,
+                  tau=0.5 if variables == H.VARS_INITIAL else 0.1, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5,
                   max_iter=args.max_iter, newton=args.newton, variables=variables)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -639,15 +645,19 @@ def run_chain_ttr(args):
         "metric": "time-to-reach solves/sec (chain workload)", "value": ok / args.steps / t, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax{args.t_max:g}_N512_{P}pts", "n": n, "m": m, "N": N,
+        "config": {"workload": f"spring_chain_n200_m10_ttr_tmax{args.t_max:g}_"
+                               f"{'fixedstep' if fixed else 'N'}{N}_{P}pts", "n": n, "m": m, "N": N,
+                   "rule": "fixed step t_max/N (one table)" if fixed else "Eq. 17 (N nodes on [0, T])",
                    "t_max": args.t_max, "tol_gap": TOL, "tol_T": 1e-5, "points": P,
-                   "variables": "paper's p" if args.paper_variables else "terminal-time q",
+                   "variables": "paper's p" if variables == H.VARS_INITIAL else "terminal-time q",
                    "search": "newton hybrid" if args.newton else "certified bisection", "rounds": steps,
                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(r["status"].cpu().numpy(),
                                                                             return_counts=True))},
                    "T_mean": float(Tv.mean()), "T_max": float(Tv.max()),
-                   "tables": "one float64 table per point and candidate horizon"},
-        "roofline": {"bound": "hbm", "kernel": "pdhg_generic_kernel<float> (per-point tables)", "achieved": None,
+                   "tables": "one float64 table on [0, t_max] for every point and candidate" if fixed else
+                             "one float64 table per point and candidate horizon"},
+        "roofline": None if fixed else
+                    {"bound": "hbm", "kernel": "pdhg_generic_kernel<float> (per-point tables)", "achieved": None,
                      "peak": measured_peaks()[0]["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None,
                      "note": "each point reads its own 4 MB float32 table twice per iteration; the step also "
                              "builds one float64 table per point and candidate"},
@@ -925,6 +935,8 @@ def main():
     ap.add_argument("--warm", action="store_true", help="secondary chain workload: learned warm start")
     ap.add_argument("--newton", action="store_true", help="chain_ttr workload: Newton hybrid instead of bisection")
     ap.add_argument("--t-max", type=float, default=40.0, help="chain_ttr workload: upper end of the bracket")
+    ap.add_argument("--ttr-rule", choices=["fixed", "paper"], default="fixed",
+                    help="chain_ttr workload: fixed-step rule with one shared table, or Eq. 17 per point")
     ap.add_argument("--train-points", type=int, default=8192, help="chain warm start: labelled training points")
     ap.add_argument("--train-epochs", type=int, default=60, help="chain warm start: training epochs")
     ap.add_argument("--max-iter", type=int, default=400000,

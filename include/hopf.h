@@ -56,6 +56,19 @@ extern "C" {
 #define HOPF_TRAPEZOID 1    /* t_i = i T/(N-1), end weights halved           */
 #define HOPF_SIMPSON 2      /* composite Simpson: N odd, t_i = i T/(N-1),
                                weights T/(3(N-1)) (1, 4, 2, 4, ..., 2, 4, 1)   */
+#define HOPF_LEFT_FIXED 3   /* left Riemann sum with the fixed step
+                               dt = t_max/N (another quadrature of the kind
+                               §III.A allows): nodes t_i = i dt with t_i < T,
+                               weights dt, the last one T - t_last; Eq. 17
+                               with k nodes at T = k dt.  Needs terminal-time
+                               variables (the table on [0, t_max] then serves
+                               every horizon), a finite t_max >= every horizon
+                               (a horizon outside [0, t_max] gets phi = NaN and
+                               HOPF_NONFINITE), n <= 512, adaptive = 0; not
+                               for hopf_value_warm, hopf_value_stacked,
+                               hopf_value_noalloc or hopf_node_table.  float32
+                               runs the tiled kernel (17 <= n <= 256) or the
+                               general one, never the tensor-core kernel.     */
 
 /* arithmetic of the iteration */
 #define HOPF_FP64 0 /* float64 everywhere                                    */
@@ -90,8 +103,9 @@ typedef struct {
 } hopf_problem;
 
 typedef struct {
-    int rule;           /* HOPF_LEFT_RIEMANN, HOPF_TRAPEZOID or HOPF_SIMPSON      */
-    int N;              /* quadrature nodes (>= 1; >= 2 trapezoid; odd >= 3 Simpson) */
+    int rule;           /* HOPF_LEFT_RIEMANN, _TRAPEZOID, _SIMPSON or _LEFT_FIXED */
+    int N;              /* quadrature nodes (>= 1; >= 2 trapezoid; odd >= 3 Simpson;
+                           fixed step: nodes on [0, t_max]) */
     int max_iter;       /* iteration cap per solve                                */
     int gap_every;      /* duality-gap check period g (>= 1)                      */
     int precision;      /* HOPF_FP64 or HOPF_FP32                                 */

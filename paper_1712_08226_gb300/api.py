@@ -12,7 +12,7 @@ import numpy as np
 from . import _lib
 
 BALL, BOX = 0, 1
-LEFT_RIEMANN, TRAPEZOID, SIMPSON = 0, 1, 2
+LEFT_RIEMANN, TRAPEZOID, SIMPSON, LEFT_FIXED = 0, 1, 2, 3
 FP64, FP32 = 0, 1
 VARS_INITIAL, VARS_TERMINAL = 0, 1
 STATUS = {0: "ok", 1: "max_iter", 2: "nonfinite", 3: "unreachable", 4: "ambiguous_sign"}

@@ -32,7 +32,7 @@ long long tile_workspace_floats(int n, int m, int N, int ppt, int grid);
 cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm, const float *x,
                              const float *p_init, float *phi, float *pstar, float *gap, int *iters, int *status,
                              float *ws, int *queue, int ppt, int grid, size_t smem, int dbuf, float *carry_st,
-                             int *carry_list, cudaStream_t s);
+                             int *carry_list, cudaStream_t s, float *Pout = nullptr, float *Dout = nullptr);
 long long tile_carry_floats(int n, int m, int N, int ppt, int P);
 bool tc_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *grid);
 long long tc_workspace_floats(int n, int m, int N, int grid);
@@ -42,7 +42,21 @@ cudaError_t launch_pdhg_tc(const float *inst, const double *inst64, const SolveP
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
-                                       double *out64, float *out32, double *scratch, int need_eig, int terminal);
+                                       double *out64, float *out32, double *scratch, int need_eig, int terminal,
+                                       double *gram_snap, int snap);
+int fixed_powers_count(int N);
+cudaError_t launch_fixed_lam(const double *snaps, int nsnap, int n, double *lam, double *scratch, cudaStream_t s);
+cudaError_t launch_fixed_powers(const double *A, int n, double dt, int J, double *Ep, double *Em, double *scratch,
+                                cudaStream_t s);
+template <typename R>
+cudaError_t launch_fixed_prep(int P, const double *Tv, int t_stride, double t_max, double dt, int N, double tau,
+                              double sigma_scale, const double *lam, int snap, const int *active, int *nk,
+                              double *wl, double *sig, int n, R *phi, R *pstar, R *gap, int *iters, int *status,
+                              cudaStream_t s);
+template <typename R>
+cudaError_t launch_fixed_map(int mode, int P, int n, const double *A, double anorm, const double *pw, int J,
+                             const int *nk, const double *wl, const R *in, R *out, const int *active, int sms,
+                             cudaStream_t s);
 template <typename R>
 cudaError_t launch_to_terminal(const double *inst64, int n, int m, int N, int inst_stride, int P, const R *x,
                                const R *p0, R *xq, R *q0, const int *active, cudaStream_t s);
@@ -158,6 +172,27 @@ __global__ void order_scatter_kernel(int P, const int *bucket, int *cursor, int 
 __global__ void failed_points_kernel(int P, const int *status, int *list, int *count) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P && status[k] != HOPF_OK) list[atomicAdd(count, 1)] = k;
+}
+
+// list of the active points (order unspecified)
+__global__ void active_points_kernel(int P, const int *active, int *list, int *count) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P && active[k]) list[atomicAdd(count, 1)] = k;
+}
+
+// dst row k = src row k for the active points (all when active is null)
+template <typename R>
+__global__ void copy_rows_kernel(int P, int n, const int *active, const R *src, R *dst) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)P * n) return;
+    const int k = (int)(e / n);
+    if (!active || active[k]) dst[e] = src[e];
+}
+template <typename R>
+cudaError_t launch_copy_rows(int P, int n, const int *active, const R *src, R *dst, cudaStream_t s) {
+    const long long total = (long long)P * n;
+    copy_rows_kernel<R><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, n, active, src, dst);
+    return cudaGetLastError();
 }
 }  // namespace hopf
 
@@ -305,7 +340,9 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
     if (!is_spd(pr->W, pr->n)) return fail(HOPF_ENOTSPD, "W is not symmetric positive definite");
     if (o->precision != HOPF_FP64 && o->precision != HOPF_FP32) return fail(HOPF_EINVAL, "bad precision");
     if (need_solver) {
-        if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID && o->rule != HOPF_SIMPSON) return fail(HOPF_EINVAL, "bad rule");
+        if (o->rule != HOPF_LEFT_RIEMANN && o->rule != HOPF_TRAPEZOID && o->rule != HOPF_SIMPSON &&
+            o->rule != HOPF_LEFT_FIXED)
+            return fail(HOPF_EINVAL, "bad rule");
         if (o->N < 1 || (o->rule == HOPF_TRAPEZOID && o->N < 2) ||
             (o->rule == HOPF_SIMPSON && (o->N < 3 || o->N % 2 == 0)) || o->N > (1 << 20))
             return fail(HOPF_EINVAL, "bad node count N=%d", o->N);
@@ -322,6 +359,14 @@ int check_problem(const hopf_problem *pr, const hopf_opts *o, bool need_solver) 
             return fail(HOPF_EINVAL, "variables must be HOPF_VARS_INITIAL or HOPF_VARS_TERMINAL");
         if (o->adaptive != 0 && o->adaptive != 1) return fail(HOPF_EINVAL, "adaptive must be 0 or 1");
         if (o->adaptive && o->accel) return fail(HOPF_EINVAL, "adaptive and accel exclude each other");
+        if (o->rule == HOPF_LEFT_FIXED) {
+            if (o->variables != HOPF_VARS_TERMINAL)
+                return fail(HOPF_EINVAL, "the fixed-step rule needs terminal-time variables");
+            if (!(o->t_max > 0.0) || !std::isfinite(o->t_max))
+                return fail(HOPF_EINVAL, "the fixed-step rule needs a finite t_max > 0");
+            if (o->adaptive) return fail(HOPF_EINVAL, "the fixed-step rule runs fixed step sizes (adaptive = 0)");
+            if (pr->n > 512) return fail(HOPF_EINVAL, "the fixed-step rule supports n <= 512");
+        }
     }
     return HOPF_SUCCESS;
 }
@@ -508,7 +553,7 @@ int launch_tables(const DevProblem &d, const hopf_problem *pr, const hopf_opts *
                   cudaStream_t s) {
     CU(launch_build_instances_opt(grid, table_threads(pr->n), s, d.A, d.B, d.q, d.W, Tv, active, n_inst, pr->n,
                                   pr->m, o->N, o->rule, o->tau, o->sigma_scale, inst64, inst32, scratch,
-                                  o->accel || o->adaptive, o->variables == HOPF_VARS_TERMINAL));
+                                  o->accel || o->adaptive, o->variables == HOPF_VARS_TERMINAL, nullptr, 0));
     return HOPF_SUCCESS;
 }
 
@@ -916,6 +961,347 @@ int ttr_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, 
     return HOPF_SUCCESS;
 }
 
+// ------------------------------------------------- fixed-step quadrature rule
+// One table on [0, t_max] in terminal-time variables (N nodes, step
+// dt = t_max / N) serves every point and horizon: the node count, last weight
+// and dual step of each point's horizon come from fixed_prep, the maps of
+// the query point and of p from the binary powers of e^{+-dt A}.
+struct FixedCtx {
+    int N = 0, nsnap = 0, J = 0;
+    double dt = 0.0, anorm = 0.0;
+    double *Tm = nullptr, *i64 = nullptr, *tsc = nullptr, *snaps = nullptr, *lam = nullptr, *lsc = nullptr;
+    double *Ep = nullptr, *Em = nullptr, *psc = nullptr, *wl = nullptr, *sig = nullptr;
+    float *i32 = nullptr;
+    int *nk = nullptr;
+};
+
+template <typename AR>
+FixedCtx take_fixed(AR &a, int n, int m, int N, int P, bool fp32) {
+    FixedCtx f;
+    const InstanceLayout L = InstanceLayout::make(n, m, N);
+    f.N = N;
+    f.nsnap = (N + FX_SNAP - 1) / FX_SNAP;
+    f.J = fixed_powers_count(N);
+    f.Tm = a.template take<double>(1);
+    f.i64 = a.template take<double>((size_t)L.stride);
+    f.i32 = fp32 ? a.template take<float>((size_t)L.stride) : nullptr;
+    f.tsc = a.template take<double>((size_t)table_scratch_doubles(n, m));
+    f.snaps = a.template take<double>((size_t)f.nsnap * n * n);
+    f.lam = a.template take<double>((size_t)f.nsnap);
+    f.lsc = a.template take<double>((size_t)f.nsnap * (2 * n + 8));
+    f.Ep = a.template take<double>((size_t)f.J * n * n);
+    f.Em = a.template take<double>((size_t)f.J * n * n);
+    f.psc = a.template take<double>((size_t)2 * (2 * n * n + 8));
+    f.nk = a.template take<int>((size_t)P);
+    f.wl = a.template take<double>((size_t)P);
+    f.sig = a.template take<double>((size_t)P);
+    return f;
+}
+
+// the shared table at t_max with its prefix |K|^2 values, and the powers
+int fixed_setup(FixedCtx &f, const DevProblem &d, const hopf_problem *pr, const hopf_opts *o, cudaStream_t s) {
+    const int n = pr->n, m = pr->m;
+    f.dt = o->t_max / (double)o->N;
+    double r1 = 0.0, ri = 0.0;          // |A|_1 and |A|_inf bound the sub-steps of the remainder series
+    for (int a = 0; a < n; ++a) {
+        double cs = 0.0, rs = 0.0;
+        for (int b = 0; b < n; ++b) {
+            cs += std::fabs(pr->A[b * n + a]);
+            rs += std::fabs(pr->A[a * n + b]);
+        }
+        r1 = std::max(r1, cs);
+        ri = std::max(ri, rs);
+    }
+    f.anorm = std::max(r1, ri);
+    CU(cudaMemcpyAsync(f.Tm, &o->t_max, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(launch_build_instances_opt(1, table_threads(n), s, d.A, d.B, d.q, d.W, f.Tm, nullptr, 1, n, m, o->N,
+                                  HOPF_LEFT_RIEMANN, o->tau, o->sigma_scale, f.i64, f.i32, f.tsc, o->accel, 1,
+                                  f.snaps, FX_SNAP));
+    CU(launch_fixed_lam(f.snaps, f.nsnap, n, f.lam, f.lsc, s));
+    CU(launch_fixed_powers(d.A, n, f.dt, f.J, f.Ep, f.Em, f.psc, s));
+    return HOPF_SUCCESS;
+}
+
+// tiled kernel for float32 states of 17..256 components, else the general one
+bool fixed_tile(const hopf_problem *pr, const hopf_opts *o, int P, const Device &dev, int *ppt, int *grid,
+                size_t *smem, int *dbuf) {
+    return o->precision == HOPF_FP32 && pr->n > 16 && o->kernel != HOPF_KERNEL_GENERIC &&
+           tile_plan(pr->n, pr->m, o->N, P, dev.sms, dev.smem_optin - 2048, ppt, grid, smem, dbuf);
+}
+
+template <typename R>
+int value_fixed_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *t_,
+                     int t_stride, const void *pinit_, void *phi_, void *pstar_, void *gap_, int *iters,
+                     int *status, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const bool fp32 = o->precision == HOPF_FP32;
+    const bool hio = o->host_io != 0;
+    const int nT = t_stride ? P : 1;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
+    size_t tile_smem = 0;
+    const bool tile = fixed_tile(pr, o, P, dev, &tile_ppt, &tile_grid, &tile_smem, &tile_dbuf);
+    FixedCtx f;
+    DevProblem d;
+    double *Tv;
+    R *dx, *dt, *dpi, *dphi, *dps, *dgap, *xq, *q0, *qs, *y;
+    int *dit, *dst, *ctr, *tcl;
+    float *tws, *tcs;
+    auto plan = [&](Arena &a) {
+        d = take_problem(a, n, m);
+        f = take_fixed(a, n, m, N, P, fp32);
+        Tv = a.template take<double>(nT);
+        dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
+        dt = hio ? a.template take<R>((size_t)nT) : (R *)t_;
+        dpi = (hio && pinit_) ? a.template take<R>((size_t)P * n) : (R *)pinit_;
+        dphi = hio ? a.template take<R>(P) : (R *)phi_;
+        dps = hio ? a.template take<R>((size_t)P * n) : (R *)pstar_;
+        dgap = hio ? a.template take<R>(P) : (R *)gap_;
+        dit = hio ? a.template take<int>(P) : iters;
+        dst = hio ? a.template take<int>(P) : status;
+        xq = a.template take<R>((size_t)P * n);
+        q0 = pinit_ ? a.template take<R>((size_t)P * n) : nullptr;
+        qs = a.template take<R>((size_t)P * n);
+        y = tile ? nullptr : a.template take<R>((size_t)P * N * m);
+        ctr = a.template take<int>(4);
+        tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
+        tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base, s);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    rc = upload_problem(d, pr, s);
+    if (rc) return rc;
+    if (hio) {
+        CU(cudaMemcpyAsync(dx, x_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dt, t_, sizeof(R) * nT, cudaMemcpyHostToDevice, s));
+        if (pinit_) CU(cudaMemcpyAsync(dpi, pinit_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+    }
+    CU(launch_horizons(nT, s, dt, fp32, Tv));
+    rc = fixed_setup(f, d, pr, o, s);
+    if (rc) return rc;
+    CU(launch_fixed_prep<R>(P, Tv, t_stride, o->t_max, f.dt, N, o->tau, o->sigma_scale, f.lam, FX_SNAP, nullptr,
+                            f.nk, f.wl, f.sig, n, dphi, dps, dgap, dit, dst, s));
+    CU(launch_fixed_map<R>(0, P, n, d.A, f.anorm, f.Ep, f.J, f.nk, f.wl, dx, xq, nullptr, dev.sms, s));
+    if (pinit_) CU(launch_fixed_map<R>(2, P, n, d.A, f.anorm, f.Em, f.J, f.nk, f.wl, dpi, q0, nullptr, dev.sms, s));
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.warm = pinit_ != nullptr;
+    prm.fx_nk = f.nk;
+    prm.fx_wl = f.wl;
+    prm.fx_sig = f.sig;
+    if (tile) {
+        CU(launch_pdhg_tile(f.i32, f.i64, prm, (const float *)xq, (const float *)q0, (float *)dphi, (float *)qs,
+                            (float *)dgap, dit, dst, tws, ctr, tile_ppt, tile_grid, tile_smem, tile_dbuf, tcs, tcl,
+                            s));
+    } else {
+        const R *inst = fp32 ? (const R *)f.i32 : (const R *)f.i64;
+        rc = launch_generic<R>(inst, prm, xq, q0, dphi, qs, dgap, dit, dst, nullptr, nullptr, y, nullptr, s);
+        if (rc) return rc;
+    }
+    CU(launch_fixed_map<R>(1, P, n, d.A, f.anorm, f.Ep, f.J, f.nk, f.wl, qs, dps, nullptr, dev.sms, s));
+    if (hio) {
+        CU(cudaMemcpyAsync(phi_, dphi, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(pstar_, dps, sizeof(R) * P * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(gap_, dgap, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(iters, dit, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status, dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return HOPF_SUCCESS;
+}
+
+template <typename R>
+int ttr_fixed_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *Tlo_,
+                   const void *Thi_, const void *pinit_, void *Tstar_, void *pstar_, void *gap_, int *status,
+                   int *steps_out, cudaStream_t s) {
+    const int n = pr->n, m = pr->m, N = o->N;
+    const bool fp32 = o->precision == HOPF_FP32;
+    const bool hio = o->host_io != 0;
+    const bool wb = Tlo_ && Thi_;
+    Device dev;
+    int rc = query_device(&dev);
+    if (rc) return rc;
+    int tile_ppt = 0, tile_grid = 0, tile_dbuf = 0;
+    size_t tile_smem = 0;
+    const bool tile = fixed_tile(pr, o, P, dev, &tile_ppt, &tile_grid, &tile_smem, &tile_dbuf);
+    FixedCtx f;
+    struct Bufs {
+        DevProblem d;
+        double *lo, *hi, *cand, *Tf;
+        int *phase, *warm, *st, *act, *sst, *fst, *its, *rem, *list, *ctr, *tcl;
+        R *Pv, *Dv, *phi, *gtmp, *ptmp, *xq, *q0, *qlast, *qout, *y;
+        R *dx, *dlo, *dhi, *dpi, *dTs, *dps, *dgap;
+        int *dst;
+        float *tws, *tcs;
+    } b;
+    auto plan = [&](Arena &a) {
+        b.d = take_problem(a, n, m);
+        f = take_fixed(a, n, m, N, P, fp32);
+        b.lo = a.template take<double>(P);
+        b.hi = a.template take<double>(P);
+        b.cand = a.template take<double>(P);
+        b.Tf = a.template take<double>(P);
+        b.phase = a.template take<int>(P);
+        b.warm = a.template take<int>(P);
+        b.st = a.template take<int>(P);
+        b.act = a.template take<int>(P);
+        b.sst = a.template take<int>(P);
+        b.fst = a.template take<int>(P);
+        b.its = a.template take<int>(P);
+        b.rem = a.template take<int>(4);
+        b.list = a.template take<int>(P);
+        b.ctr = a.template take<int>(4);
+        b.Pv = a.template take<R>(P);
+        b.Dv = a.template take<R>(P);
+        b.phi = a.template take<R>(P);
+        b.gtmp = a.template take<R>(P);
+        b.ptmp = a.template take<R>((size_t)P * n);
+        b.xq = a.template take<R>((size_t)P * n);
+        b.q0 = pinit_ ? a.template take<R>((size_t)P * n) : nullptr;
+        b.qlast = a.template take<R>((size_t)P * n);
+        b.qout = a.template take<R>((size_t)P * n);
+        b.y = tile ? nullptr : a.template take<R>((size_t)P * N * m);
+        b.tws = tile ? a.template take<float>((size_t)tile_workspace_floats(n, m, N, tile_ppt, tile_grid)) : nullptr;
+        b.tcs = tile ? a.template take<float>((size_t)tile_carry_floats(n, m, N, tile_ppt, P)) : nullptr;
+        b.tcl = tile ? a.template take<int>((size_t)2 * P) : nullptr;
+        b.dx = hio ? a.template take<R>((size_t)P * n) : (R *)x_;
+        b.dlo = (hio && wb) ? a.template take<R>(P) : (R *)Tlo_;
+        b.dhi = (hio && wb) ? a.template take<R>(P) : (R *)Thi_;
+        b.dpi = (hio && pinit_) ? a.template take<R>((size_t)P * n) : (R *)pinit_;
+        b.dTs = hio ? a.template take<R>(P) : (R *)Tstar_;
+        b.dps = hio ? a.template take<R>((size_t)P * n) : (R *)pstar_;
+        b.dgap = hio ? a.template take<R>(P) : (R *)gap_;
+        b.dst = hio ? a.template take<int>(P) : status;
+    };
+    Arena meas(nullptr);
+    plan(meas);
+    void *base = nullptr;
+    rc = ensure_workspace(meas.off, &base, s);
+    if (rc) return rc;
+    Arena a(base);
+    plan(a);
+    rc = upload_problem(b.d, pr, s);
+    if (rc) return rc;
+    if (hio) {
+        CU(cudaMemcpyAsync(b.dx, x_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+        if (wb) {
+            CU(cudaMemcpyAsync(b.dlo, Tlo_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(b.dhi, Thi_, sizeof(R) * P, cudaMemcpyHostToDevice, s));
+        }
+        if (pinit_) CU(cudaMemcpyAsync(b.dpi, pinit_, sizeof(R) * P * n, cudaMemcpyHostToDevice, s));
+    }
+    rc = fixed_setup(f, b.d, pr, o, s);
+    if (rc) return rc;
+    // V' = W^-1 of the shared table is the T = 0 test of the target (Eq. 34)
+    CU(launch_ttr_init<R>(P, s, f.i64, n, m, N, b.dx, wb ? b.dlo : nullptr, wb ? b.dhi : nullptr, o->t_max, b.lo,
+                          b.hi, b.phase, b.warm, b.st, b.Tf));
+    SolveParams prm;
+    fill_params(prm, pr, o, P);
+    prm.fx_nk = f.nk;
+    prm.fx_wl = f.wl;
+    prm.fx_sig = f.sig;
+    // one solve of the active points at the horizons Tv: the rule data of
+    // each horizon, the query point mapped to e^{TA} x, solution q into qout
+    // (copied to qlast), P and D into Pv, Dv.  The first solve starts from
+    // the user's p_init mapped to q0 = e^{-TA^T} p_init (cold without it);
+    // every later one from the point's last solution in qlast (zero for a
+    // point inside the target, solved only at T = 0).
+    bool first = true;
+    CU(cudaMemsetAsync(b.qlast, 0, sizeof(R) * P * n, s));
+    auto solve = [&](const double *Tv, const int *act, int sign_mode, R *gap_o, int *st_o) -> int {
+        CU(launch_fixed_prep<R>(P, Tv, 1, o->t_max, f.dt, N, o->tau, o->sigma_scale, f.lam, FX_SNAP, act, f.nk, f.wl,
+                                f.sig, n, (R *)nullptr, (R *)nullptr, (R *)nullptr, nullptr, nullptr, s));
+        CU(launch_fixed_map<R>(0, P, n, b.d.A, f.anorm, f.Ep, f.J, f.nk, f.wl, b.dx, b.xq, act, dev.sms, s));
+        const R *p0 = first ? nullptr : b.qlast;
+        if (first && b.dpi) {
+            CU(launch_fixed_map<R>(2, P, n, b.d.A, f.anorm, f.Em, f.J, f.nk, f.wl, b.dpi, b.q0, act, dev.sms, s));
+            p0 = b.q0;
+        }
+        first = false;
+        R *q_out = b.qout;
+        SolveParams q = prm;
+        q.warm = p0 != nullptr;
+        q.sign_mode = sign_mode;
+        if (tile) {
+            CU(cudaMemsetAsync(b.ctr, 0, sizeof(int), s));
+            if (act) {
+                active_points_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, act, b.list, b.ctr);
+                CU(cudaGetLastError());
+                q.list = b.list;
+                q.list_count = b.ctr;
+            }
+            CU(launch_pdhg_tile(f.i32, f.i64, q, (const float *)b.xq, (const float *)p0, (float *)b.phi,
+                                (float *)q_out, (float *)gap_o, b.its, st_o, b.tws, b.ctr + 1, tile_ppt, tile_grid,
+                                tile_smem, tile_dbuf, b.tcs, b.tcl, s, (float *)b.Pv, (float *)b.Dv));
+        } else {
+            const R *inst = fp32 ? (const R *)f.i32 : (const R *)f.i64;
+            int r = launch_generic<R>(inst, q, b.xq, p0, b.phi, q_out, gap_o, b.its, st_o, b.Pv, b.Dv, b.y, act, s);
+            if (r) return r;
+        }
+        // the next solve starts from this one's solution
+        CU(launch_copy_rows<R>(P, n, act, b.qout, b.qlast, s));
+        return HOPF_SUCCESS;
+    };
+    int steps = 0;
+    const int max_steps = o->max_steps > 0 ? o->max_steps : 256;
+    int remaining = 0;
+    if (o->newton) {
+        // hybrid Newton/bisection of §IV; the derivative d phi / dT = -H_x
+        // needs p* in the paper's variable: p = e^{T A^T} q
+        CU(launch_ttr_newton_start(P, s, b.hi, b.phase, b.cand, b.act));
+        for (;;) {
+            rc = solve(b.cand, b.act, 1, b.gtmp, b.sst);
+            if (rc) return rc;
+            CU(launch_fixed_map<R>(1, P, n, b.d.A, f.anorm, f.Ep, f.J, f.nk, f.wl, b.qout, b.ptmp, b.act, dev.sms, s));
+            CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
+            CU(launch_ttr_newton_update<R>(P, s, n, m, pr->ctrl_kind, b.d.A, b.d.B, b.d.q, b.dx, o->t_max, o->tol_T,
+                                           b.Pv, b.Dv, b.ptmp, b.cand, b.act, b.lo, b.hi, b.phase, b.st, b.Tf,
+                                           b.rem));
+            CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            ++steps;
+            if (remaining == 0 || steps >= max_steps) break;
+        }
+    } else {
+        for (;;) {
+            CU(launch_ttr_candidates(P, s, b.lo, b.hi, b.phase, b.cand, b.act));
+            rc = solve(b.cand, b.act, 1, b.gtmp, b.sst);
+            if (rc) return rc;
+            CU(cudaMemsetAsync(b.rem, 0, sizeof(int), s));
+            CU(launch_ttr_update<R>(P, s, o->t_max, o->tol_T, b.cand, b.act, b.Pv, b.Dv, b.sst, b.lo, b.hi,
+                                    b.phase, b.warm, b.st, b.Tf, b.rem));
+            CU(cudaMemcpyAsync(&remaining, b.rem, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            ++steps;
+            if (remaining == 0 || steps >= max_steps) break;
+        }
+    }
+    if (remaining > 0) CU(launch_ttr_cap(P, s, b.hi, b.phase, b.st, b.Tf));
+    // final certified solve at T* (T = 0 inside the target, t_max if
+    // unreachable), p* = e^{T* A^T} q*
+    rc = solve(b.Tf, nullptr, 0, b.dgap, b.fst);
+    if (rc) return rc;
+    CU(launch_fixed_map<R>(1, P, n, b.d.A, f.anorm, f.Ep, f.J, f.nk, f.wl, b.qout, b.dps, nullptr, dev.sms, s));
+    CU(launch_ttr_finish<R>(P, s, b.st, b.fst, b.Tf, b.dTs, b.dst));
+    if (hio) {
+        CU(cudaMemcpyAsync(Tstar_, b.dTs, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(pstar_, b.dps, sizeof(R) * P * n, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(gap_, b.dgap, sizeof(R) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status, b.dst, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    if (steps_out) *steps_out = steps;
+    return HOPF_SUCCESS;
+}
+
 // --------------------------------------------------------- hopf_trajectory
 template <typename R>
 int traj_impl(const hopf_problem *pr, const hopf_opts *o, int P, const void *x_, const void *T_,
@@ -1235,6 +1621,11 @@ int hopf_value(const hopf_problem *prob, const hopf_opts *opts, int P, const voi
     if (t_stride != 0 && t_stride != 1) return fail(HOPF_EINVAL, "t_stride must be 0 or 1");
     if (!x || !t || !phi || !p_star || !gap || !iters || !status) return fail(HOPF_EINVAL, "null array");
     cudaStream_t s = (cudaStream_t)stream;
+    if (opts->rule == HOPF_LEFT_FIXED) {
+        if (opts->precision == HOPF_FP64)
+            return value_fixed_impl<double>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+        return value_fixed_impl<float>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
+    }
     if (opts->precision == HOPF_FP64)
         return value_impl<double>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
     return value_impl<float>(prob, opts, P, x, t, t_stride, p_init, phi, p_star, gap, iters, status, s);
@@ -1288,6 +1679,11 @@ int hopf_time_to_reach(const hopf_problem *prob, const hopf_opts *opts, int P, c
     if ((T_lo == nullptr) != (T_hi == nullptr)) return fail(HOPF_EINVAL, "give both T_lo and T_hi or neither");
     if (!x || !T_star || !p_star || !gap || !status) return fail(HOPF_EINVAL, "null array");
     cudaStream_t s = (cudaStream_t)stream;
+    if (opts->rule == HOPF_LEFT_FIXED) {
+        if (opts->precision == HOPF_FP64)
+            return ttr_fixed_impl<double>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
+        return ttr_fixed_impl<float>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
+    }
     if (opts->precision == HOPF_FP64)
         return ttr_impl<double>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
     return ttr_impl<float>(prob, opts, P, x, T_lo, T_hi, p_init, T_star, p_star, gap, status, steps, s);
@@ -1314,6 +1710,7 @@ int hopf_node_table(const hopf_problem *prob, const hopf_opts *opts, double T, d
     int rc = check_problem(prob, opts, true);
     if (rc) return rc;
     if (!(T >= 0.0) || !std::isfinite(T)) return fail(HOPF_EINVAL, "T must be finite and >= 0");
+    if (opts->rule == HOPF_LEFT_FIXED) return fail(HOPF_EINVAL, "node table: give one of the T / N rules");
     if (!K || !w) return fail(HOPF_EINVAL, "null array");
     return node_table_impl(prob, opts, T, K, w, (cudaStream_t)stream);
 }
@@ -1385,6 +1782,7 @@ int hopf_value_warm(const hopf_problem *prob, const hopf_opts *opts, const hopf_
     rc = check_mlp(net);
     if (rc) return rc;
     if (opts->adaptive) return fail(HOPF_EINVAL, "warm start: adaptive steps are not supported");
+    if (opts->rule == HOPF_LEFT_FIXED) return fail(HOPF_EINVAL, "warm start: the fixed-step rule is not supported");
     if (opts->precision != HOPF_FP32) return fail(HOPF_EINVAL, "warm start: FP32 only");
     if (net->n_in != prob->n || net->n_out != prob->n) return fail(HOPF_EINVAL, "network must map R^n to R^n");
     if (P < 0 || (t_stride != 0 && t_stride != 1) || max_iter_warm < 0) return fail(HOPF_EINVAL, "bad P/t_stride");

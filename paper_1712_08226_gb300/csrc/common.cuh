@@ -69,8 +69,16 @@ struct SolveParams {
     float *in_st, *out_st;    // [slot][CARRY_W] p, pbar, tau, sigma, iteration count
     int *in_list, *out_list;  // point index of each slot
     int *in_count, *out_count;
+    // fixed-step rule: per point node count (-1: horizon out of range, point
+    // skipped), last node weight and dual step; null for the other rules
+    const int *fx_nk;
+    const double *fx_wl, *fx_sig;
     double tau, tol_gap, sign_floor;
 };
+
+// fixed-step rule: prefix Gram sums (and their largest eigenvalues) every
+// FX_SNAP nodes
+constexpr int FX_SNAP = 64;
 
 // float64 scratch (elements) one thread block needs to build one instance
 __host__ __device__ inline long long table_scratch_doubles(int n, int m) {

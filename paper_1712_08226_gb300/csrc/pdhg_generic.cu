@@ -30,6 +30,10 @@
 // al.): tau /= (1 - a), sigma *= (1 - a) when |r_p| > 1.5 |r_d|, the reverse
 // when 1.5 |r_p| < |r_d|, a *= 0.95 after a change; the prox of G is then
 // taken at the current tau through M = U diag(lam) U^T.
+//
+// Fixed-step rule (prm.fx_nk set): one table on [0, t_max] in terminal-time
+// variables; point k uses its first fx_nk[k] nodes, the last one weighted
+// fx_wl[k], and its own dual step fx_sig[k] (nodes beyond take no part).
 #include "common.cuh"
 
 namespace hopf {
@@ -69,7 +73,12 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     const R *I = inst_base + (prm.inst_stride ? (long long)k * L.stride : 0LL);
     const R *K = I + L.K, *w = I + L.w, *M = I + L.M, *V = I + L.V, *S = I + L.S, *sc = I + L.sc;
-    R sigma = sc[SC_SIGMA];
+    const bool fx = prm.fx_nk != nullptr;
+    const int Nk = fx ? prm.fx_nk[k] : N;
+    if (Nk < 0) return;                                        // horizon out of range: outputs already set
+    const R wlast = fx ? (R)prm.fx_wl[k] : R(0);
+    auto wt = [&](int i) -> R { return (fx && i == Nk - 1) ? wlast : w[i]; };
+    R sigma = fx ? (R)prm.fx_sig[k] : sc[SC_SIGMA];
     const R gamma = sc[SC_GAMMA];
     const bool zero = sc[SC_ZERO] != R(0);
     R tau = (R)prm.tau;
@@ -109,7 +118,7 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     }
     __syncwarp();
     // y0: K p0 (cold, §VI) or w_i argmax_U <c, K_i p0> (warm)
-    for (int i = lane; i < N; i += 32) {
+    for (int i = lane; i < Nk; i += 32) {
         R t[GEN_MMAX];
         const R *Ki = K + (long long)i * m * n;
         R nrm2 = 0;
@@ -119,7 +128,7 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
             t[c] = s;
             nrm2 = fma(s, s, nrm2);
         }
-        R wi = w[i];
+        R wi = wt(i);
         for (int c = 0; c < m; ++c) {
             R v = t[c];
             if (prm.warm) {
@@ -133,7 +142,7 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
     if (prm.adaptive) {
         for (int j = lane; j < n; j += 32) {
             R s = 0;
-            for (int i = 0; i < N; ++i)
+            for (int i = 0; i < Nk; ++i)
                 for (int c = 0; c < m; ++c) s = fma(K[((long long)i * m + c) * n + j], y[(long long)i * m + c], s);
             accp[j] = s;
         }
@@ -150,11 +159,11 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
         for (int j = lane; j < n; j += 32) qv[j] = sigma * pb[j];
         __syncwarp();
         R hs = 0, dy2 = 0;
-        for (int i = lane; i < N; i += 32) {
+        for (int i = lane; i < Nk; i += 32) {
             R t[GEN_MMAX];
             const R *Ki = K + (long long)i * m * n;
             R *yi = y + (long long)i * m;
-            const R wi = w[i];
+            const R wi = wt(i);
             R nt = 0, nu = 0;
             for (int c = 0; c < m; ++c) {
                 R s = 0;
@@ -204,7 +213,7 @@ __global__ void pdhg_generic_kernel(const R *__restrict__ inst_base, SolveParams
         // K^T y: lanes over state components, sum over nodes
         for (int j = lane; j < n; j += 32) {
             R s = 0;
-            for (int i = 0; i < N; ++i) {
+            for (int i = 0; i < Nk; ++i) {
                 const R *Ki = K + (long long)i * m * n;
                 const R *yi = y + (long long)i * m;
                 for (int c = 0; c < m; ++c) s = fma(Ki[c * n + j], yi[c], s);

@@ -33,6 +33,15 @@
 // point whose float64 gap passes is accepted (phi = -P in float64); otherwise
 // it iterates on with its float32 acceptance threshold halved.  The slot of an
 // accepted point takes the next point from a global queue.
+//
+// Time-to-reach sign mode (prm.sign_mode): a point also stops once the sign
+// of phi is certified, P < 0 (phi > 0) or D > 0 (phi < 0); a float32 margin of
+// the slot's tolerance nominates it and the float64 evaluation decides.  P
+// and D of every finished point go to Pout / Dout when given.
+//
+// Fixed-step rule (prm.fx_nk set): the table covers [0, t_max]; a slot uses
+// the first fx_nk nodes of its point (the last weighted fx_wl) and its own
+// dual step fx_sig; a block streams only the node blocks its slots need.
 #include "common.cuh"
 
 namespace hopf {
@@ -108,7 +117,8 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                  const float *__restrict__ x, const float *__restrict__ p_init, float *__restrict__ phi,
                  float *__restrict__ pstar, float *__restrict__ gap_out, int *__restrict__ iters,
                  int *__restrict__ status, float *__restrict__ slot_p, float *__restrict__ slot_x,
-                 float *__restrict__ slot_y, int *__restrict__ queue, int dbuf) {
+                 float *__restrict__ slot_y, int *__restrict__ queue, int dbuf, float *__restrict__ Pout,
+                 float *__restrict__ Dout) {
     constexpr int NPT = MP >= 8 ? 1 : 8 / MP;
     constexpr int RW = NPT * MP;
     constexpr int PT = 32 * PPT;
@@ -156,8 +166,10 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     float *Qs = Hs + PT, *Ds = Qs + PT;
     __shared__ int sl_pt[PT], sl_cnt[PT], sl_fresh[PT], sl_done[PT];
     __shared__ float sl_tol[PT], sl_tau[PT], sl_sig[PT];
-    __shared__ int s_check, s_active, s_verify, s_park;
-    __shared__ int sl_park[PT];
+    __shared__ int s_check, s_active, s_verify, s_park, s_nch;
+    __shared__ int sl_park[PT], sl_nk[PT];
+    __shared__ float sl_wl[PT], sl_mg[PT];
+    const bool fx = prm.fx_nk != nullptr;
     __shared__ double red[TILE_WARPS];
 
     float *ps = slot_p + (long long)blockIdx.x * n4 * PT;          // [n4][pt]
@@ -168,8 +180,20 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
     // the queue walks points 0..P-1, or list[0 .. *list_count) when given
     const int Pq = prm.list ? *prm.list_count : P;
     auto take = [&]() -> int {
-        const int q = atomicAdd(queue, 1);
-        return q < Pq ? (prm.list ? prm.list[q] : q) : -1;
+        for (;;) {
+            const int q = atomicAdd(queue, 1);
+            if (q >= Pq) return -1;
+            const int k = prm.list ? prm.list[q] : q;
+            if (!fx || prm.fx_nk[k] >= 0) return k;     // out-of-range horizons are skipped
+        }
+    };
+    // per-slot node count, last weight and dual step of its point
+    auto slot_rule = [&](int s) {
+        const int k = sl_pt[s];
+        const bool f = fx && k >= 0;
+        sl_nk[s] = f ? prm.fx_nk[k] : N;
+        sl_wl[s] = f ? (float)prm.fx_wl[k] : 0.f;
+        sl_sig[s] = f ? (float)prm.fx_sig[k] : sc[SC_SIGMA];
     };
     // fill every slot from the queue
     if (tid < PT) {
@@ -178,8 +202,9 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         sl_fresh[tid] = 1;
         sl_done[tid] = 0;
         sl_tol[tid] = (float)prm.tol_gap;
+        sl_mg[tid] = (float)prm.tol_gap;
         sl_tau[tid] = (float)prm.tau;
-        sl_sig[tid] = sc[SC_SIGMA];
+        slot_rule(tid);
     }
     __syncthreads();
     for (int e = tid; e < n4 * PT; e += blockDim.x) {
@@ -205,18 +230,21 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
         }
         __syncthreads();
         if (tid == 0) {
-            int chk = (git % prm.gap_every) == 0, act = 0;
+            int chk = (git % prm.gap_every) == 0, act = 0, nmax = 0;
             for (int s = 0; s < PT; ++s)
                 if (sl_pt[s] >= 0) {
                     ++act;
                     if (sl_cnt[s] > prm.max_iter) chk = 1;
+                    nmax = max(nmax, sl_nk[s]);
                 }
             s_check = chk;
             s_active = act;
+            s_nch = fx ? (nmax + NC - 1) / NC : g.chunks;      // node blocks the slots need
         }
         __syncthreads();
         if (s_active == 0) break;
         const bool check = s_check != 0;
+        const int nch = s_nch;
 
         float4 R[PPT][NQW];
 #pragma unroll
@@ -236,10 +264,10 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             cp_async_commit();
         };
         if (dbuf) load_block(0, Kbuf0);
-        for (int c = 0; c < g.chunks; ++c) {
+        for (int c = 0; c < nch; ++c) {
             if (dbuf) {
                 Ks = (c & 1) ? Kbuf1 : Kbuf0;
-                if (c + 1 < g.chunks) {
+                if (c + 1 < nch) {
                     load_block(c + 1, (c & 1) ? Kbuf0 : Kbuf1);
                     cp_async_wait<1>();
                 } else {
@@ -255,12 +283,13 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             float ypre[PPT][RW];
 #pragma unroll
             for (int t = 0; t < NPT; ++t) {
-                const bool node_ok = c * NC + warp * NPT + t < N;
+                const int i = c * NC + warp * NPT + t;
+                const bool node_ok = i < N;
                 const long long grow = (long long)c * CR + warp * RW + t * MP;
 #pragma unroll
                 for (int pp = 0; pp < PPT; ++pp) {
                     const int s = lane + 32 * pp;
-                    const bool ld = node_ok && sl_pt[s] >= 0 && !sl_fresh[s];
+                    const bool ld = node_ok && i < sl_nk[s] && sl_pt[s] >= 0 && !sl_fresh[s];
 #pragma unroll
                     for (int cc = 0; cc < MP; ++cc) ypre[pp][t * MP + cc] = ld ? Yg[(grow + cc) * PT + s] : 0.f;
                 }
@@ -292,7 +321,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             for (int t = 0; t < NPT; ++t) {
                 const int i = c * NC + warp * NPT + t;
                 const bool node_ok = i < N;
-                const float wi = node_ok ? __ldg(wv + i) : 0.f;
+                const float wtab = node_ok ? __ldg(wv + i) : 0.f;
                 const int row = warp * RW + t * MP;
                 const long long grow = (long long)c * CR + row;
 #pragma unroll
@@ -300,6 +329,9 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                     const int s = lane + 32 * pp;
                     float yn[MP];
                     if (node_ok && sl_pt[s] >= 0) {
+                        // weight of node i for this slot's horizon
+                        const int nks = sl_nk[s];
+                        const float wi = !fx ? wtab : (i < nks - 1 ? wtab : (i == nks - 1 ? sl_wl[s] : 0.f));
                         float nt = 0.f;
 #pragma unroll
                         for (int cc = 0; cc < MP; ++cc) {
@@ -462,6 +494,7 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                     int st = -1;
                     if (!isfinite(Pv) || !isfinite(Dv)) st = HOPF_NONFINITE;
                     else if (gp + gap_allowance(quad, H, Dv, scl) <= sl_tol[s]) st = HOPF_OK;
+                    else if (prm.sign_mode && (-Pv > sl_mg[s] * scl || Dv > sl_mg[s] * scl)) st = HOPF_OK;
                     else if (cnt > prm.max_iter) st = HOPF_MAXITER;
                     if (st == HOPF_OK) {
                         sl_done[s] = 2;             // float64 re-certification below
@@ -470,6 +503,8 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                         gap_out[k] = gp;
                         iters[k] = cnt - 1;
                         status[k] = st;
+                        if (Pout) Pout[k] = Pv;
+                        if (Dout) Dout[k] = Dv;
                         sl_done[s] = 1;
                     }
                 }
@@ -487,9 +522,11 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
             double *ub = reinterpret_cast<double *>(Ys);            // n doubles (dual block is free here)
             for (int s = 0; s < PT; ++s) {
                 if (sl_done[s] != 2) continue;                        // uniform: shared memory
+                const int nks = sl_nk[s];
+                const double wl64 = fx ? prm.fx_wl[sl_pt[s]] : 0.0;
                 // H = sum_i w_i |K_i pbar|_*
                 double hp = 0.0;
-                for (int i = tid; i < N; i += blockDim.x) {
+                for (int i = tid; i < nks; i += blockDim.x) {
                     double nt = 0.0;
                     for (int c = 0; c < m; ++c) {
                         const double *Kr = K64 + ((long long)i * m + c) * n;
@@ -497,13 +534,13 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                         for (int j = 0; j < n; ++j) z = fma(Kr[j], (double)pb_at(j, s), z);
                         nt += ball ? z * z : fabs(z);
                     }
-                    hp = fma(w64[i], ball ? sqrt(nt) : nt, hp);
+                    hp = fma((fx && i == nks - 1) ? wl64 : w64[i], ball ? sqrt(nt) : nt, hp);
                 }
                 const double H64 = block_sum(hp, red);
                 // u = x0 - K^T y (y shrunk into w_i U), then D = 1 - u^T V u
                 for (int j = tid; j < n; j += blockDim.x) {
                     double r = 0.0;
-                    for (int i = 0; i < N; ++i)
+                    for (int i = 0; i < nks; ++i)
                         for (int c = 0; c < m; ++c)
                             r = fma(K64[((long long)i * m + c) * n + j],
                                     (double)Yg[((long long)i * MP + c) * PT + s], r);
@@ -526,16 +563,20 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                 const double g64 = rel_gap(P64, D64);
                 const double scl = fmax(1.0, fmax(fabs(P64), fabs(D64)));
                 if (tid == 0) {
-                    if (g64 + gap_allowance(quad64, H64, D64, scl) <= prm.tol_gap) {
+                    if (g64 + gap_allowance(quad64, H64, D64, scl) <= prm.tol_gap ||
+                        (prm.sign_mode && (P64 < 0.0 || D64 > 0.0))) {
                         const int k = sl_pt[s];
                         phi[k] = (float)(-P64);
                         gap_out[k] = (float)g64;
                         iters[k] = sl_cnt[s] - 1;
                         status[k] = HOPF_OK;
+                        if (Pout) Pout[k] = (float)P64;
+                        if (Dout) Dout[k] = (float)D64;
                         sl_done[s] = 1;
                     } else {
                         sl_done[s] = 0;
-                        sl_tol[s] *= 0.5f;
+                        sl_tol[s] *= 0.5f;           // stricter float32 gap,
+                        sl_mg[s] *= 2.f;             // wider float32 sign margin
                     }
                 }
                 __syncthreads();
@@ -641,8 +682,9 @@ pdhg_tile_kernel(const float *__restrict__ inst, const double *__restrict__ inst
                 sl_cnt[s] = 0;
                 sl_fresh[s] = 1;
                 sl_tol[s] = (float)prm.tol_gap;
+                sl_mg[s] = (float)prm.tol_gap;
                 sl_tau[s] = (float)prm.tau;
-                sl_sig[s] = sc[SC_SIGMA];
+                slot_rule(s);
             } else {
                 sl_fresh[s] = 0;
                 if (prm.accel && sl_pt[s] >= 0) {
@@ -726,7 +768,8 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                       const float *__restrict__ Kp, const float *__restrict__ Sp, SolveParams prm, int ppt,
                       const float *__restrict__ x, float *__restrict__ phi, float *__restrict__ pstar,
                       float *__restrict__ gap_out, int *__restrict__ iters, int *__restrict__ status,
-                      const float *__restrict__ slot_y, int *__restrict__ queue2) {
+                      const float *__restrict__ slot_y, int *__restrict__ queue2, float *__restrict__ Pout,
+                      float *__restrict__ Dout) {
     const int n = prm.n, m = prm.m, N = prm.N;
     const TileGeom g = tile_geom(n, m, N, ppt);
     const int n4 = g.n4, nq = g.nq, MPd = g.mp, PT = g.pt;
@@ -778,13 +821,21 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
         const int k = prm.out_list[2 * e], loc = prm.out_list[2 * e + 1];
         const float *Yp = slot_y + (long long)(loc / PT) * G * PT + (loc % PT);
         const float *st = prm.out_st + (long long)e * CW;
+        // node count and last weight of this point's horizon (fixed-step rule)
+        const int nkv = prm.fx_nk ? prm.fx_nk[k] : N;
+        const int Gk = nkv * MPd;                      // table rows in use
+        const double wl64 = prm.fx_nk ? prm.fx_wl[k] : 0.0;
+        auto wt = [&](int i) -> float {
+            return (prm.fx_nk && i == nkv - 1) ? (float)wl64 : __ldg(wv + i);
+        };
         for (int j = tid; j < n4; j += nt) {
             pb[j] = st[j];
             pp[j] = st[n4 + j];
             x0[j] = j < n ? x[(long long)k * n + j] : 0.f;
         }
-        for (int r = tid; r < G; r += nt) ys[r] = Yp[(long long)r * PT];
+        for (int r = tid; r < G; r += nt) ys[r] = r < Gk ? Yp[(long long)r * PT] : 0.f;
         float tau = st[2 * n4], sigma = st[2 * n4 + 1], tol = st[2 * n4 + 3];
+        float mg = (float)prm.tol_gap * ((float)prm.tol_gap / fmaxf(tol, 1e-30f));   // sign margin: doubles as tol halves
         int cnt = (int)st[2 * n4 + 2];
         __syncthreads();
         for (;;) {
@@ -792,8 +843,8 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
             const bool check = (cnt % prm.gap_every) == 0 || cnt > prm.max_iter;
             // dual step, threads over nodes
             float hp = 0.f;
-            for (int i = tid; i < N; i += nt) {
-                const float wi = __ldg(wv + i);
+            for (int i = tid; i < nkv; i += nt) {
+                const float wi = wt(i);
                 float z[16];
                 float nz = 0.f;
                 for (int c = 0; c < m; ++c) {
@@ -818,7 +869,7 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
             // K^T y, threads over state components
             for (int j = tid; j < n4; j += nt) {
                 float r = 0.f;
-                for (int row = 0; row < G; ++row) r = fmaf(__ldg(Kp + (long long)row * n4 + j), ys[row], r);
+                for (int row = 0; row < Gk; ++row) r = fmaf(__ldg(Kp + (long long)row * n4 + j), ys[row], r);
                 vb[j] = fmaf(tau, x0[j] - r, pp[j]);
                 ub[j] = x0[j] - r;
             }
@@ -843,13 +894,14 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                 int stt = -1;
                 if (!isfinite(Pv) || !isfinite(Dv)) stt = HOPF_NONFINITE;
                 else if (gp + gap_allowance(quad, H, Dv, scl) <= tol) stt = HOPF_OK;
+                else if (prm.sign_mode && (-Pv > mg * scl || Dv > mg * scl)) stt = HOPF_OK;
                 else if (cnt > prm.max_iter) stt = HOPF_MAXITER;
                 if (stt == HOPF_OK) {
                     // float64 re-certification
                     const double *K64 = inst64 + L.K, *M64 = inst64 + L.M, *V64 = inst64 + L.V;
                     const double *w64 = inst64 + L.w;
                     double h64 = 0.0;
-                    for (int i = tid; i < N; i += nt) {
+                    for (int i = tid; i < nkv; i += nt) {
                         double nz = 0.0;
                         for (int c = 0; c < m; ++c) {
                             const double *Kr = K64 + ((long long)i * m + c) * n;
@@ -857,7 +909,7 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                             for (int j = 0; j < n; ++j) z = fma(Kr[j], (double)pb[j], z);
                             nz += ball ? z * z : fabs(z);
                         }
-                        h64 = fma(w64[i], ball ? sqrt(nz) : nz, h64);
+                        h64 = fma((prm.fx_nk && i == nkv - 1) ? wl64 : w64[i], ball ? sqrt(nz) : nz, h64);
                     }
                     const double H64 = block_sum(h64, red);
                     double q64 = 0.0, d64 = 0.0;
@@ -865,7 +917,7 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                     // after the dual rows in shared memory
                     for (int j = tid; j < n; j += nt) {
                         double r = 0.0;
-                        for (int i = 0; i < N; ++i)
+                        for (int i = 0; i < nkv; ++i)
                             for (int c = 0; c < m; ++c)
                                 r = fma(K64[((long long)i * m + c) * n + j], (double)ys[i * MPd + c], r);
                         reinterpret_cast<double *>(ys + G)[j] = (double)x0[j] - (1.0 - 4e-7) * r;
@@ -886,16 +938,20 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                     const double P64 = quad64 + H64;
                     const double g64 = rel_gap(P64, D64);
                     const double s64 = fmax(1.0, fmax(fabs(P64), fabs(D64)));
-                    if (g64 + gap_allowance(quad64, H64, D64, s64) <= prm.tol_gap) {
+                    if (g64 + gap_allowance(quad64, H64, D64, s64) <= prm.tol_gap ||
+                        (prm.sign_mode && (P64 < 0.0 || D64 > 0.0))) {
                         if (tid == 0) {
                             phi[k] = (float)(-P64);
                             gap_out[k] = (float)g64;
                             iters[k] = cnt - 1;
                             status[k] = HOPF_OK;
+                            if (Pout) Pout[k] = (float)P64;
+                            if (Dout) Dout[k] = (float)D64;
                         }
                         done = true;
                     } else {
                         tol *= 0.5f;
+                        mg *= 2.f;
                         if (cnt > prm.max_iter) stt = HOPF_MAXITER;
                     }
                     __syncthreads();
@@ -906,6 +962,8 @@ pdhg_tile_tail_kernel(const float *__restrict__ inst, const double *__restrict__
                         gap_out[k] = gp;
                         iters[k] = cnt - 1;
                         status[k] = stt;
+                        if (Pout) Pout[k] = Pv;
+                        if (Dout) Dout[k] = Dv;
                     }
                     done = true;
                 }
@@ -978,13 +1036,13 @@ template <int MP, int PPT>
 static cudaError_t launch_tile_t(const float *inst, const double *inst64, const float *Kp, const float *Sp, const float *Mp,
                                  const float *Vp, const SolveParams &prm, const float *x, const float *p_init,
                                  float *phi, float *pstar, float *gap, int *iters, int *status, float *sp,
-                                 float *sx, float *sy, int *queue, int grid, size_t smem, int dbuf,
-                                 cudaStream_t s) {
+                                 float *sx, float *sy, int *queue, int grid, size_t smem, int dbuf, float *Pout,
+                                 float *Dout, cudaStream_t s) {
     auto kern = pdhg_tile_kernel<MP, PPT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, TILE_WARPS * 32, smem, s>>>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters,
-                                             status, sp, sx, sy, queue, dbuf);
+                                             status, sp, sx, sy, queue, dbuf, Pout, Dout);
     return cudaGetLastError();
 }
 
@@ -1007,7 +1065,7 @@ long long tile_carry_floats(int n, int m, int N, int ppt, int P) {
 cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const SolveParams &prm_in, const float *x,
                              const float *p_init, float *phi, float *pstar, float *gap, int *iters, int *status,
                              float *ws, int *queue, int ppt, int grid, size_t smem, int dbuf, float *carry_st,
-                             int *carry_list, cudaStream_t s) {
+                             int *carry_list, cudaStream_t s, float *Pout, float *Dout) {
     const int n = prm_in.n, m = prm_in.m, N = prm_in.N;
     const TileGeom g = tile_geom(n, m, N, ppt);
     const size_t tsmem = tile_tail_smem(n, m, N, ppt);
@@ -1031,9 +1089,9 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
 #define TILE_CASE(MPV)                                                                                        \
     case MPV:                                                                                                 \
         e = ppt == 2 ? launch_tile_t<MPV, 2>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                             status, sp, sx, sy, queue, grid, smem, dbuf, s)                    \
+                                             status, sp, sx, sy, queue, grid, smem, dbuf, Pout, Dout, s)        \
                      : launch_tile_t<MPV, 1>(inst, inst64, Kp, Sp, Mp, Vp, prm, x, p_init, phi, pstar, gap, iters, \
-                                             status, sp, sx, sy, queue, grid, smem, dbuf, s);                   \
+                                             status, sp, sx, sy, queue, grid, smem, dbuf, Pout, Dout, s);       \
         break;
     switch (g.mp) {
         TILE_CASE(1)
@@ -1056,7 +1114,7 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
         if (e != cudaSuccess) return e;
     }
     pdhg_tile_tail_kernel<<<4 * grid, 256, tsmem, s>>>(inst, inst64, Kp, Sp, prm, ppt, x, phi, pstar, gap, iters,
-                                                        status, sy, queue + 1);
+                                                        status, sy, queue + 1, Pout, Dout);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                                        int n_inst, int n, int m, int N, int rule, double tau,
                                        double sigma_scale, double *out64, float *out32,
                                        double *scratch, bool smem_scratch, int w_count, int need_eig,
-                                       int terminal) {
+                                       int terminal, double *gram_snap, int snap) {
     const InstanceLayout L = InstanceLayout::make(n, m, N);
     // scratch in shared memory when the launch provides it (small n), else global
     extern __shared__ double tsm[];
@@ -77,6 +77,10 @@ __global__ void build_instances_kernel(const double *__restrict__ A, const doubl
                 C[e] += s;
             }
             __syncthreads();
+            // fixed-step rule (terminal variables, nodes in time order): the
+            // prefix Gram sum of the first idx + 1 nodes every snap nodes
+            if (gram_snap && terminal && ((idx + 1) % snap == 0 || idx == N - 1))
+                cta::copy(gram_snap + (long long)(idx / snap) * n * n, C, n * n);
         }
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             double wi = h;
@@ -193,21 +197,23 @@ cudaError_t launch_build_instances(int grid, int threads, cudaStream_t s, const 
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
                                                                       tau, sigma_scale, out64, out32, scratch, in_smem, 1,
-                                                                      1, 0);
+                                                                      1, 0, nullptr, 0);
     return cudaGetLastError();
 }
 
 // as launch_build_instances, with the eigen-decomposition of M (used only by
-// the accelerated iteration) optional and the choice of variables
+// the accelerated iteration) optional, the choice of variables and, for the
+// fixed-step rule, the prefix Gram sums every snap nodes (gram_snap, null: off)
 cudaError_t launch_build_instances_opt(int grid, int threads, cudaStream_t s, const double *A, const double *B,
                                        const double *qd, const double *W, const double *Tv, const int *active,
                                        int n_inst, int n, int m, int N, int rule, double tau, double sigma_scale,
-                                       double *out64, float *out32, double *scratch, int need_eig, int terminal) {
+                                       double *out64, float *out32, double *scratch, int need_eig, int terminal,
+                                       double *gram_snap, int snap) {
     const size_t bytes = sizeof(double) * (size_t)table_scratch_doubles(n, m);
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, active, n_inst, n, m, N, rule,
                                                                       tau, sigma_scale, out64, out32, scratch, in_smem, 1,
-                                                                      need_eig, terminal);
+                                                                      need_eig, terminal, gram_snap, snap);
     return cudaGetLastError();
 }
 
@@ -220,7 +226,7 @@ cudaError_t launch_build_instances_wblocks(int grid, int threads, cudaStream_t s
     const bool in_smem = bytes <= 48 * 1024;
     build_instances_kernel<<<grid, threads, in_smem ? bytes : 0, s>>>(A, B, qd, W, Tv, nullptr, n_inst, n, m, N,
                                                                       rule, tau, sigma_scale, out64, out32, scratch,
-                                                                      in_smem, w_count, 0, 0);
+                                                                      in_smem, w_count, 0, 0, nullptr, 0);
     return cudaGetLastError();
 }
 

@@ -139,12 +139,66 @@ def chain200_time_to_reach(P=2):
          T=r["T"], status=r["status"], steps=r["steps"])
 
 
+def chain200_fixed_values():
+    # the fixed-step rule at the chain's full size: one table on [0, 40] with
+    # dt = 40/2048 (the paper's step at T = 10, N = 512), horizons between
+    # multiples of the step (a partial last node), terminal-time variables
+    w = wl.workload_chain(8)
+    rule = oh.FixedStep(40.0, 2048)
+    rows = []
+    for T, idx in ((3.3, [0, 1]), (17.77, [2, 3])):
+        r = oh.value(w["system"], w["x"][idx], T, 2048, rule, tau=0.1, tol=1e-7, max_iter=2000000,
+                     variables="terminal")
+        assert np.all(r["status"] == oh.OK)
+        rows += [(k, T, r["phi"][j], r["gap"][j]) for j, k in enumerate(idx)]
+    dump("chain200_fixed_values.json",
+         dict(source="oracle.hopf.value (FixedStep(40, 2048), variables=terminal)",
+              workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, points idx",
+              t_max=40.0, N=2048, rule="fixed_step", tau=0.1, oracle_tol=1e-7),
+         idx=[r[0] for r in rows], T=[r[1] for r in rows], phi=[r[2] for r in rows], gap=[r[3] for r in rows])
+
+
+def chain200_fixed_time_to_reach(P=2):
+    # time-to-reach at the chain's full size with the fixed-step rule
+    # (dt = 40/2048), terminal-time variables, the first P chain points
+    w = wl.workload_chain(P)
+    r = oh.time_to_reach(w["system"], w["x"], 40.0, 2048, oh.FixedStep(40.0, 2048), tau=0.1, tol_T=1e-6,
+                         tol_gap=1e-5, max_iter=400000, variables="terminal")
+    dump("chain200_fixed_time_to_reach.json",
+         dict(source="oracle.hopf.time_to_reach (FixedStep(40, 2048), variables=terminal)",
+              workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, first P points",
+              P=P, t_max=40.0, N=2048, rule="fixed_step", tau=0.1, oracle_tol_T=1e-6),
+         T=r["T"], status=r["status"], steps=r["steps"])
+
+
+def chain10_fixed_time_to_reach():
+    # fixed-step rule (dt = 20/256) on the 10-mass chain (n = 20, m = 2 box),
+    # three of 24 seeded points, terminal-time variables
+    sysd = wl.spring_chain(masses=10, actuators=2, radius_target=1.0)
+    x = wl.normal_points(11, 24, 20, 0.7)
+    idx = [0, 7, 23]
+    r = oh.time_to_reach(sysd, x[idx], 20.0, 256, oh.FixedStep(20.0, 256), tau=0.2, tol_T=1e-7, tol_gap=1e-8,
+                         variables="terminal")
+    assert np.all(r["status"] == oh.OK)
+    dump("chain10_fixed_time_to_reach.json",
+         dict(source="oracle.hopf.time_to_reach (FixedStep(20, 256), variables=terminal)",
+              workload="10-mass spring chain (n=20, m=2 box), r=1, x~N(0,0.49 I) seed 11, 24 points, idx",
+              P=24, t_max=20.0, N=256, rule="fixed_step", tau=0.2, oracle_tol_T=1e-7),
+         idx=idx, T=r["T"], status=r["status"])
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["random10", "di", "ttr", "box", "chain10", "unscented", "chain200", "random128"]
     if "chain200" in which:
         chain_values()
     if "chain200_ttr" in which:
         chain200_time_to_reach()
+    if "chain10_fixed_ttr" in which:
+        chain10_fixed_time_to_reach()
+    if "chain200_fixed" in which:
+        chain200_fixed_values()
+    if "chain200_fixed_ttr" in which:
+        chain200_fixed_time_to_reach()
     if "random128" in which:
         random128_values()
     if "unscented" in which:
