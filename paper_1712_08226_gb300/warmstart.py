@@ -141,22 +141,3 @@ def value_warm(system, x, t, net, opts=None, max_iter_warm=None, stream=None):
     out["n_fallback"] = nfb
     return out
 
-
-def time_to_reach_warm(system, x, net, opts=None, delta=0.05, stream=None):
-    """Time to reach (§IV) seeded by a network that predicts (p*, T*) from x
-    (n + 1 outputs): the search starts on the bracket [T^(1 - delta),
-    T^(1 + delta)] and every inner solve from p^ (both passed to
-    hopf_time_to_reach, which checks the two bracket ends and falls back to
-    [0, t_max] when the prediction misses).  Returns the dict of
-    api.time_to_reach plus the prediction."""
-    from .api import time_to_reach
-    n = system.n
-    pred = net.forward(x.contiguous())
-    p_hat = pred[:, :n].contiguous()
-    T_hat = pred[:, n].clamp_min(1e-6)
-    t_max = (opts or Options()).t_max
-    lo = (T_hat * (1.0 - delta)).clamp(0.0, t_max).contiguous()
-    hi = (T_hat * (1.0 + delta)).clamp(1e-6, t_max).contiguous()
-    out = time_to_reach(system, x, opts, T_lo=lo, T_hi=hi, p_init=p_hat, stream=stream)
-    out["T_hat"] = T_hat
-    return out
