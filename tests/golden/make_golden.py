@@ -125,20 +125,6 @@ def random128_values(P=8):
          phi=r["phi"], p=r["p"], gap=r["gap"])
 
 
-def chain200_time_to_reach(P=2):
-    # time-to-reach at the chain's full size (n = 200, m = 10 box, N = 512),
-    # terminal-time variables (the same T*; the paper's variable needs ~20x
-    # more iterations here), the first P points of the chain workload
-    w = wl.workload_chain(P)
-    r = oh.time_to_reach(w["system"], w["x"], 40.0, w["N"], w["rule"], tau=0.1, tol_T=1e-6, tol_gap=1e-5,
-                         max_iter=400000, variables="terminal")
-    dump("chain200_time_to_reach.json",
-         dict(source="oracle.hopf.time_to_reach (variables=terminal)",
-              workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, first P points",
-              P=P, t_max=40.0, N=w["N"], rule="left_riemann", tau=0.1, oracle_tol_T=1e-6),
-         T=r["T"], status=r["status"], steps=r["steps"])
-
-
 def chain200_fixed_values():
     # the fixed-step rule at the chain's full size: one table on [0, 40] with
     # dt = 40/2048 (the paper's step at T = 10, N = 512), horizons between
@@ -156,19 +142,6 @@ def chain200_fixed_values():
               workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, points idx",
               t_max=40.0, N=2048, rule="fixed_step", tau=0.1, oracle_tol=1e-7),
          idx=[r[0] for r in rows], T=[r[1] for r in rows], phi=[r[2] for r in rows], gap=[r[3] for r in rows])
-
-
-def chain200_fixed_time_to_reach(P=2):
-    # time-to-reach at the chain's full size with the fixed-step rule
-    # (dt = 40/2048), terminal-time variables, the first P chain points
-    w = wl.workload_chain(P)
-    r = oh.time_to_reach(w["system"], w["x"], 40.0, 2048, oh.FixedStep(40.0, 2048), tau=0.1, tol_T=1e-6,
-                         tol_gap=1e-5, max_iter=400000, variables="terminal")
-    dump("chain200_fixed_time_to_reach.json",
-         dict(source="oracle.hopf.time_to_reach (FixedStep(40, 2048), variables=terminal)",
-              workload="100-mass spring chain (n=200, m=10 box, r=0.5), x~N(0,I) seed 3, first P points",
-              P=P, t_max=40.0, N=2048, rule="fixed_step", tau=0.1, oracle_tol_T=1e-6),
-         T=r["T"], status=r["status"], steps=r["steps"])
 
 
 def chain10_fixed_time_to_reach():
@@ -191,14 +164,10 @@ if __name__ == "__main__":
     which = sys.argv[1:] or ["random10", "di", "ttr", "box", "chain10", "unscented", "chain200", "random128"]
     if "chain200" in which:
         chain_values()
-    if "chain200_ttr" in which:
-        chain200_time_to_reach()
     if "chain10_fixed_ttr" in which:
         chain10_fixed_time_to_reach()
     if "chain200_fixed" in which:
         chain200_fixed_values()
-    if "chain200_fixed_ttr" in which:
-        chain200_fixed_time_to_reach()
     if "random128" in which:
         random128_values()
     if "unscented" in which:

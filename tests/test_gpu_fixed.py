@@ -190,24 +190,6 @@ def test_fixed_step_time_to_reach_fp32_chain_tile(H, newton):
     assert np.all(np.abs(T - Tg) <= 1e-4 * Tg), (T, Tg)
 
 
-def test_fixed_step_time_to_reach_chain200_full_size(H):
-    # the bench's launch: the 100-mass chain (n = 200), one table on [0, 40]
-    # of 2048 nodes, tiled kernel, 64 points; the first two against the oracle
-    name = os.path.join(GOLD, "chain200_fixed_time_to_reach.json")
-    if not os.path.exists(name):
-        pytest.skip("stored values not generated")
-    g = gold("chain200_fixed_time_to_reach.json")
-    w = wl.workload_chain(64)
-    opts = H.Options(rule=H.LEFT_FIXED, N=2048, t_max=40.0, tau=0.1, tol_gap=1e-5, tol_T=1e-5, newton=True,
-                     max_iter=400000, variables=TERM)
-    r = H.time_to_reach(H.System.from_dict(w["system"]), cuda(w["x"]), opts)
-    st = r["status"].cpu().numpy()
-    assert np.all(np.isin(st, (0, 4))), np.unique(st, return_counts=True)
-    Tg = np.array(g["T"])
-    T = np_(r["T"])[:Tg.size]
-    assert np.all(np.abs(T - Tg) <= 1e-4 * Tg), (T, Tg)
-
-
 def test_fixed_step_rejects_paper_variables_and_adaptive(H):
     sysd = H.System.from_dict(wl.double_integrator(0.1))
     with pytest.raises(H.HopfError):
