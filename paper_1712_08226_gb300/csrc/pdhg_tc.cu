@@ -560,6 +560,14 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
             float *pbn = pbs + (long long)(par ^ 1) * TC_PTS * n1 + tid;
             for (int b = 0; b < nblk; ++b) {
                 const long long gb = (long long)it * nblk + b;
+                // this block's dual rows first: their global-memory latency
+                // overlaps the wait for the K pbar product
+                float yv[TC_NB];
+                const long long R0 = (long long)b * TC_NB;
+                if (pt >= 0 && !fresh) {
+#pragma unroll
+                    for (int e = 0; e < TC_NB; ++e) yv[e] = yrow[(R0 + e) * TC_PTS];
+                }
                 tc_wait(&mb_d1f[gb & 1], (uint32_t)((gb >> 1) & 1), &s_fail);
                 tc::fence_after_sync();
                 float z[TC_NB];
@@ -572,12 +580,6 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
                 }
                 tc::fence_before_sync();
                 mbar_arrive(&mb_d1e[gb & 1]);             // GEMM1 of block b + 2 may overwrite it
-                float yv[TC_NB];
-                const long long R0 = (long long)b * TC_NB;
-                if (pt >= 0 && !fresh) {
-#pragma unroll
-                    for (int e = 0; e < TC_NB; ++e) yv[e] = yrow[(R0 + e) * TC_PTS];
-                }
                 constexpr int NPB = TC_NB / MP;
 #pragma unroll
                 for (int t = 0; t < NPB; ++t) {
