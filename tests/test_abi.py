@@ -140,3 +140,30 @@ def test_stacked_entry_validates_before_touching_a_device(lib):
     assert call(np.stack([0.1 * np.eye(2)] * 65)) == -1          # at most 64 copies
     assert call(good, dict(accel=True)) == -1
     assert call(good, P=0) == 0                                    # empty batch: nothing to do
+
+
+def test_python_constants_match_header_defines():
+    from paper_1712_08226_gb300 import api
+    src = open(os.path.join(ROOT, "include", "hopf.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+HOPF_([A-Z0-9_]+)\s+(-?\d+)\b", src)}
+    pairs = {"LEFT_RIEMANN": api.LEFT_RIEMANN, "TRAPEZOID": api.TRAPEZOID, "SIMPSON": api.SIMPSON,
+             "LEFT_FIXED": api.LEFT_FIXED, "BALL": api.BALL, "BOX": api.BOX, "FP32": api.FP32,
+             "FP64": api.FP64, "VARS_INITIAL": api.VARS_INITIAL, "VARS_TERMINAL": api.VARS_TERMINAL}
+    for name, val in pairs.items():
+        assert defines[name] == val, name
+
+
+def test_fixed_step_rule_validates_before_touching_a_device(lib):
+    # the fixed-step rule needs terminal-time variables, a finite t_max and
+    # fixed step sizes; unknown rules are refused
+    from inputs import workloads as wl
+    sysd = wl.double_integrator(0.1)
+    assert _call_value(lib, sysd, dict(rule=3, N=16, t_max=2.0)) == -1
+    assert b"terminal-time" in lib.hopf_last_error()
+    assert _call_value(lib, sysd, dict(rule=3, N=16, t_max=float("inf"), variables=1)) == -1
+    assert b"t_max" in lib.hopf_last_error()
+    assert _call_value(lib, sysd, dict(rule=3, N=16, t_max=2.0, variables=1, adaptive=True)) == -1
+    assert _call_value(lib, sysd, dict(rule=4, N=16)) == -1
+    assert b"bad rule" in lib.hopf_last_error()
+    # a valid fixed-step request with no points needs no device
+    assert _call_value(lib, sysd, dict(rule=3, N=16, t_max=2.0, variables=1), P=0) == 0
