@@ -303,8 +303,18 @@ SECONDARY = {
     "dimension": dict(points=16384, T=2.5, d=120, cpu_points=2),
     # the first --systems of the 64 random systems (n = 4..128, m = ceil(n/8),
     # 1000-4000 points each, t = 2, N = 256), solved one system per call
-    "ragged": dict(T=2.0, N=256, tau=0.15, cpu_points=1),
+    # (terminal-time variables unless --paper-variables: tau 0.5 for n <= 16,
+    # 1.0 above, from an oracle sweep of 0.15-6 on four of the systems)
+    "ragged": dict(T=2.0, N=256, tau=0.15, tau_small=0.5, tau_large=1.0, cpu_points=1),
 }
+
+
+def ragged_tau(cfg, n, paper_variables):
+    """Primal step of one ragged system: the paper's variable keeps one tau;
+    terminal-time variables take 0.5 for n <= 16 and 1.0 above."""
+    if paper_variables:
+        return cfg["tau"]
+    return cfg["tau_small"] if n <= 16 else cfg["tau_large"]
 
 
 def run_secondary(args):
@@ -337,10 +347,12 @@ def run_secondary(args):
         wname = f"ragged_random_systems_first{len(items)}_of_64_N256_t2_{points}pts"
         kernel = "pdhg_tile_kernel (n > 16) / pdhg_small_kernel (n <= 16)"
         s0 = items[0]["system"]
+        tau0 = ragged_tau(cfg, s0["A"].shape[0], args.paper_variables)
         cpu_code = (f"from inputs import workloads as wl\nfrom oracle import hopf as oh\n"
                     f"it = wl.workload_ragged()['items'][0]\nt0 = time.perf_counter()\n"
                     f"r = oh.value(it['system'], it['x'][:{cfg['cpu_points']}], {T}, {N}, oh.LEFT_RIEMANN, "
-                    f"tau={tau}, tol={TOL}, max_iter=200000)\n"
+                    f"tau={tau0}, tol={TOL}, max_iter=200000, "
+                    f"variables={'initial' if args.paper_variables else 'terminal'!r})\n"
                     f"print(json.dumps(dict(dt=time.perf_counter() - t0, ok=int((r['status'] == 0).sum()))))\n")
         x = None
     else:
@@ -522,7 +534,10 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
     import torch
     xs = [torch.tensor(it["x"], dtype=torch.float32, device="cuda") for it in items]
     systems = [H.System.from_dict(it["system"]) for it in items]
-    opts = H.Options(N=N, tau=tau, tol_gap=TOL, max_iter=args.max_iter, profile=True)
+    variables = H.VARS_INITIAL if args.paper_variables else H.VARS_TERMINAL
+    taus = [ragged_tau(cfg, S.n, args.paper_variables) for S in systems]
+    opts_of = [H.Options(N=N, tau=tu, tol_gap=TOL, max_iter=args.max_iter, profile=True, variables=variables)
+               for tu in taus]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -538,7 +553,7 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
             st = side[i % len(side)]
             st.wait_event(ev0)
             with torch.cuda.stream(st):
-                out.append(H.value(S, xd, T, opts, stream=st))
+                out.append(H.value(S, xd, T, opts_of[i], stream=st))
         for st in side:
             stream.wait_stream(st)
         return out
@@ -577,7 +592,9 @@ def run_ragged(args, H, items, cfg, cpu, rank, world, local, dist, wname, kernel
         "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded)",
-        "config": {"workload": wname, "systems": len(systems), "n_per_system": ns, "N": N, "t": T, "tau": tau,
+        "config": {"workload": wname, "systems": len(systems), "n_per_system": ns, "N": N, "t": T,
+                   "tau": "0.15" if args.paper_variables else "0.5 (n <= 16), 1.0 (n > 16)",
+                   "variables": "paper's p" if args.paper_variables else "terminal-time q",
                    "tol_gap": TOL, "points": int(sum(len(x) for x in xs)), "streams": len(side),
                    "mean_iters": float(its.mean()),
                    "max_iters": int(its.max()), "certified_per_step": ok / args.steps,
