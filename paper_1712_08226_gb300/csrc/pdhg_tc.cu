@@ -33,6 +33,13 @@
 
 namespace hopf {
 
+// the tiled kernel's tail, reused for the points this kernel parks (pdhg_tile.cu)
+long long tile_pad_floats(int n, int m, int N);
+size_t tile_tail_smem(int n, int m, int N, int ppt);
+cudaError_t launch_tile_tail_parked(const float *inst, const double *inst64, const SolveParams &prm, const float *x,
+                                    float *phi, float *pstar, float *gap, int *iters, int *status, float *ws,
+                                    const float *park_y, int *queue2, int grid, cudaStream_t s);
+
 constexpr int TC_PTS = 128;                 // slots = tensor-memory lanes = threads
 constexpr int TC_NB = 64;                   // rows of the stacked table per node block (GEMM1 N)
 constexpr int TC_KC = 32;                   // GEMM1 contraction chunk (state components)
@@ -335,13 +342,15 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
                SolveParams prm, const float *__restrict__ x, const float *__restrict__ p_init,
                float *__restrict__ phi, float *__restrict__ pstar, float *__restrict__ gap_out,
                int *__restrict__ iters, int *__restrict__ status, float *__restrict__ slots, int *queue, int *err,
-               int stages, int stage_bytes) {
+               int stages, int stage_bytes, float *__restrict__ park_st, int *__restrict__ park_list,
+               int *park_count, float *__restrict__ park_y) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t mb_full[TC_MAX_STAGES], mb_empty[TC_MAX_STAGES];
     __shared__ __align__(8) uint64_t mb_d1f[2], mb_d1e[2], mb_yf, mb_ye, mb_d2f;
     __shared__ uint32_t s_taddr;
     __shared__ int s_flag[TC_PTS];
     __shared__ volatile int s_fail;
+    __shared__ int s_park;
     __shared__ double red[4];
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -802,9 +811,48 @@ pdhg_tc_kernel(TcGeom g, TcImages im, const float *__restrict__ inst, const doub
             // before the next iteration's bulk copies
             asm volatile("fence.proxy.async;" ::: "memory");
         }
-        // iteration boundary, all threads
+        // iteration boundary, all threads (every copy and product of the
+        // iteration is complete here)
         const int any = __syncthreads_or(slot_thread && pt >= 0);
         if (any == 0 || s_fail) break;
+        // drain: the queue is empty and at most a quarter of the slots are
+        // busy.  A block-iteration costs the same with 1 or 128 busy slots, so
+        // the remaining points are parked (pbar, p, step sizes, count; the dual
+        // rows converted to the tiled layout) for the one-block-per-point tail
+        // kernel, which iterates a point with the table read from L2.
+        if (park_y) {
+            const int act = __syncthreads_count(slot_thread && pt >= 0);
+            const int fr = __syncthreads_or(slot_thread && pt >= 0 && fresh);
+            if (tid == 0)
+                s_park = (!fr && 4 * act <= TC_PTS && *reinterpret_cast<volatile int *>(queue) >= Pq) ? 1 : 0;
+            __syncthreads();
+            if (s_park) {
+                if (slot_thread && pt >= 0) {
+                    const TileGeom tg = tile_geom(n, m, N, 1);
+                    const int n4 = tg.n4, CW = 2 * n4 + 4, G = tg.chunks * tg.cr;
+                    const int e = atomicAdd(park_count, 1);
+                    park_list[2 * e] = pt;
+                    park_list[2 * e + 1] = e;
+                    float *st = park_st + (long long)e * CW;
+                    const float *pbc = pbs + (long long)par * TC_PTS * n1 + tid;     // the next iteration's pbar
+                    for (int j = 0; j < n4; ++j) {
+                        st[j] = j < n ? pbc[j * TC_PTS] : 0.f;
+                        st[n4 + j] = j < n ? prow[j * TC_PTS] : 0.f;
+                    }
+                    st[2 * n4] = tau;
+                    st[2 * n4 + 1] = sigma;
+                    st[2 * n4 + 2] = (float)cnt;
+                    st[2 * n4 + 3] = (float)prm.tol_gap;
+                    float *yd = park_y + (long long)(e / 32) * G * 32 + (e % 32);
+                    for (int i = 0; i < N; ++i) {
+                        const long long R = (long long)(i / g.npb) * TC_NB + (i % g.npb) * g.mp;
+                        for (int c = 0; c < tg.mp; ++c)
+                            yd[(long long)(i * tg.mp + c) * 32] = c < m ? yrow[(R + c) * TC_PTS] : 0.f;
+                    }
+                }
+                break;
+            }
+        }
     }
     if (s_fail) {
         if (tid == 0) atomicExch(err, 1);
@@ -841,16 +889,26 @@ bool tc_plan(int n, int m, int N, int P, int sms, size_t smem_limit, int *grid) 
     return true;
 }
 
+// points parked by the drain, for the tail kernel (the tiled kernel's layouts):
+// padded table, state records, [count, tail queue, -, -] + point list, dual rows
+static long long tc_park_floats(int n, int m, int N, int grid) {
+    const TileGeom tg = tile_geom(n, m, N, 1);
+    const long long cap = 32LL * grid;
+    return tile_pad_floats(n, m, N) + 64 + cap * (2 * tg.n4 + 4) + 64 + 4 + 2 * cap + 64 +
+           cap * (long long)tg.chunks * tg.cr + 64;
+}
+
 long long tc_workspace_floats(int n, int m, int N, int grid) {
     const TcGeom g = tc_geom(n, m, N);
     return tc_k1_floats(g) + tc_k2_floats(g) + 4LL * g.rows * g.n1 + 3LL * g.n1 + 6LL * g.n1 + 64 +
-           (long long)grid * tc_slot_floats(g) + 64;
+           (long long)grid * tc_slot_floats(g) + 64 + tc_park_floats(n, m, N, grid);
 }
 
 template <int MP>
 static cudaError_t launch_tc_t(const TcGeom &g, const TcImages &im, const float *inst, const double *inst64,
                                const SolveParams &prm, const float *x, const float *p_init, float *phi, float *pstar,
-                               float *gap, int *iters, int *status, float *slots, int *queue, int grid, cudaStream_t s) {
+                               float *gap, int *iters, int *status, float *slots, int *queue, int grid,
+                               float *park_st, int *park_list, int *park_count, float *park_y, cudaStream_t s) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -861,7 +919,8 @@ static cudaError_t launch_tc_t(const TcGeom &g, const TcImages &im, const float 
     e = cudaFuncSetAttribute(pdhg_tc_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     pdhg_tc_kernel<MP><<<grid, TC_THREADS, smem, s>>>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters,
-                                                       status, slots, queue, queue + 1, stages, sb);
+                                                       status, slots, queue, queue + 1, stages, sb, park_st, park_list,
+                                                       park_count, park_y);
     return cudaGetLastError();
 }
 
@@ -885,18 +944,50 @@ cudaError_t launch_pdhg_tc(const float *inst, const double *inst64, const SolveP
     p += 6LL * g.n1;
     p = reinterpret_cast<float *>(((uintptr_t)p + 255) & ~(uintptr_t)255);
     float *slots = p;
+    p += (long long)grid * tc_slot_floats(g);
+    // drain parking (tail kernel in the tiled layout), when its shared memory fits
+    const TileGeom tg = tile_geom(n, m, N, 1);
+    const bool park = tile_tail_smem(n, m, N, 1) <= 200 * 1024;
+    const long long cap = 32LL * grid;
+    p = reinterpret_cast<float *>(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    float *tile_ws = p;
+    p += tile_pad_floats(n, m, N);
+    p = reinterpret_cast<float *>(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    float *park_st = p;
+    p += cap * (2 * tg.n4 + 4);
+    p = reinterpret_cast<float *>(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    int *park_ctr = reinterpret_cast<int *>(p);          // [0] parked count, [1] tail queue
+    int *park_list = park_ctr + 4;
+    p += 4 + 2 * cap;
+    p = reinterpret_cast<float *>(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    float *park_y = p;
     cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(park_ctr, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     tc_prep_kernel<<<512, 256, 0, s>>>(inst64, n, m, N, g, im);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    float *pst = park ? park_st : nullptr, *py = park ? park_y : nullptr;
+    int *pl = park ? park_list : nullptr;
     switch (g.mp) {
-        case 2: return launch_tc_t<2>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, s);
-        case 4: return launch_tc_t<4>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, s);
-        case 8: return launch_tc_t<8>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, s);
-        case 10: return launch_tc_t<10>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, s);
-        default: return launch_tc_t<16>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, s);
+        case 2: e = launch_tc_t<2>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, pst, pl, park_ctr, py, s); break;
+        case 4: e = launch_tc_t<4>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, pst, pl, park_ctr, py, s); break;
+        case 8: e = launch_tc_t<8>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, pst, pl, park_ctr, py, s); break;
+        case 10: e = launch_tc_t<10>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, pst, pl, park_ctr, py, s); break;
+        default: e = launch_tc_t<16>(g, im, inst, inst64, prm, x, p_init, phi, pstar, gap, iters, status, slots, queue, grid, pst, pl, park_ctr, py, s); break;
     }
+    if (e != cudaSuccess || !park) return e;
+    // the parked points: one 256-thread block each (up to four per SM)
+    SolveParams pt = prm;
+    pt.carry_cap = 0;
+    pt.out_st = park_st;
+    pt.out_list = park_list;
+    pt.out_count = park_ctr;
+    pt.list = nullptr;
+    pt.list_count = nullptr;
+    return launch_tile_tail_parked(inst, inst64, pt, x, phi, pstar, gap, iters, status, tile_ws, park_y, park_ctr + 1,
+                                   4 * grid, s);
 }
 
 }  // namespace hopf

@@ -1118,4 +1118,37 @@ cudaError_t launch_pdhg_tile(const float *inst, const double *inst64, const Solv
     return cudaGetLastError();
 }
 
+// Tail of another solver: the padded float32 table (the tiled layout) and
+// one 256-thread block per point parked in prm.out_* (state records of
+// 2 n4 + 4 floats: pbar, p, tau, sigma, iteration count, threshold; dual rows
+// in park_y at [e / 32][row][e % 32], the tiled layout with 32 slots).  ws
+// holds tile_pad_floats(n, m, N) floats; queue2 is a zeroed device int.
+long long tile_pad_floats(int n, int m, int N) {
+    const TileGeom g = tile_geom(n, m, N, 1);
+    return (long long)g.chunks * g.cr * g.n4 + 5LL * n * g.n4;
+}
+
+cudaError_t launch_tile_tail_parked(const float *inst, const double *inst64, const SolveParams &prm, const float *x,
+                                    float *phi, float *pstar, float *gap, int *iters, int *status, float *ws,
+                                    const float *park_y, int *queue2, int grid, cudaStream_t s) {
+    const int n = prm.n, m = prm.m, N = prm.N;
+    const TileGeom g = tile_geom(n, m, N, 1);
+    const size_t tsmem = tile_tail_smem(n, m, N, 1);
+    if (tsmem > 200 * 1024) return cudaErrorInvalidValue;
+    float *Kp = ws;
+    float *Sp = Kp + (long long)g.chunks * g.cr * g.n4;
+    float *Mp = Sp + (long long)n * g.n4;
+    float *Vp = Mp + (long long)n * g.n4;
+    tile_pad_kernel<<<256, 256, 0, s>>>(inst, n, m, N, g, Kp, Sp, Mp, Vp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (tsmem > 48 * 1024) {
+        e = cudaFuncSetAttribute(pdhg_tile_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+        if (e != cudaSuccess) return e;
+    }
+    pdhg_tile_tail_kernel<<<grid, 256, tsmem, s>>>(inst, inst64, Kp, Sp, prm, 1, x, phi, pstar, gap, iters, status,
+                                                   park_y, queue2, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
 }  // namespace hopf
