@@ -35,7 +35,10 @@ closed-form double-integrator node table, an independent projected-gradient
 solver of the discrete-control problem, exhaustive active-set enumeration on
 tiny problems, the gradient identity p* = grad phi (Eq. 24), the HJ identity
 d phi / dT = -H_x (§IV), the terminal-point identity (Eq. 29) and the
-bang-bang switching-curve time of the double integrator.
+bang-bang switching-curve time of the double integrator.  The fixed-step
+rule is pinned by an independent walk of its partition, its reduction to
+Eq. 17 at multiples of the step, the single-integrator time to reach at every
+horizon and FISTA on the primal-control form with the partition's nodes.
 """
 import numpy as np
 from scipy.linalg import expm
