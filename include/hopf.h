@@ -197,7 +197,10 @@ void hopf_default_opts(hopf_opts *opts);
  *   x       [P*n]  query states (at time zero, so z0 = x, Eq. 9)
  *   t       [1] if t_stride == 0 (one horizon for every point: one shared
  *           node table), else [P] per-point horizons (t_stride == 1; one table
- *           per point).  t >= 0; t = 0 gives phi = J_x(x).
+ *           per point).  t >= 0; t = 0 gives phi = J_x(x).  With
+ *           HOPF_LEFT_FIXED one table on [0, opts->t_max] serves every
+ *           horizon; a t outside [0, t_max] gives phi = NaN, p_star = NaN and
+ *           HOPF_NONFINITE for that point.
  *   p_init  NULL (cold start of §VI: p0 = x, y0 = K x) or [P*n] warm start
  *           (p0 = p_init, y0_i = w_i argmax_{c in U} <c, K_i p0>).
  *   phi     [P]    -P(pbar): certified to lie within gap of the exact value
@@ -250,6 +253,9 @@ int hopf_value_stacked(const hopf_stacked *prob, const hopf_opts *opts, int P, c
  *   T_lo,T_hi NULL, or [P] per-point bracket (warm start: a bracket known to
  *            contain T*; a wrong bracket is detected by the two end-point signs
  *            and replaced by [0, t_max])
+ *   (HOPF_LEFT_FIXED: one float64 table on [0, t_max] for every point and
+ *   candidate, no per-point tables; each inner solve starts from the point's
+ *   previous solution, the first from p_init or cold)
  *   p_init   NULL or [P*n]: warm start of every inner solve
  *   T_star   [P]  hi at termination (0 inside the target; t_max if unreachable)
  *   p_star   [P*n] certificate primal point at T_star (solved to tol_gap)
