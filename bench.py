@@ -39,6 +39,7 @@ from inputs import workloads as wl  # noqa: E402
 METRIC = "Hopf solves/sec at gap<=1e-5: warm-start batched vs plain cold PDHG, same GB300"
 POINTS = 65536
 TOL = 1e-5
+MAX_ITER_DEFAULT = 400000
 TAU_ACCEL = 2.0
 TAU_TERM = 0.5       # Eq. 15 in terminal-time variables (oracle sweep: mean 80 iterations vs 110 at 0.3)
 # the learned warm start on the 100-mass chain (n = 200, m = 10 box, N = 512):
@@ -636,9 +637,11 @@ def run_chain_ttr(args):
     sysd = H.System.from_dict(wl.spring_chain())
     x = torch.tensor(wl.normal_points(3 + 1000 * rank, P, n, 1.0), dtype=torch.float32, device="cuda")
     variables = H.VARS_INITIAL if (args.paper_variables and not fixed) else H.VARS_TERMINAL
+    # per-solve cap: 40,000 unless given (each round waits for its slowest point)
+    max_iter = args.max_iter if args.max_iter != MAX_ITER_DEFAULT else 40000
     o = H.Options(rule=H.LEFT_FIXED if fixed else H.LEFT_RIEMANN, N=N,
                   tau=0.5 if variables == H.VARS_INITIAL else 0.1, tol_gap=TOL, t_max=args.t_max, tol_T=1e-5,
-                  max_iter=args.max_iter, newton=args.newton, variables=variables, accel=fixed)
+                  max_iter=max_iter, newton=args.newton, variables=variables, accel=fixed)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         H.time_to_reach(sysd, x, o)
@@ -672,7 +675,7 @@ def run_chain_ttr(args):
                    "status_counts": {str(k): int(v) for k, v in zip(*np.unique(r["status"].cpu().numpy(),
                                                                             return_counts=True))},
                    "T_mean": float(Tv.mean()), "T_max": float(Tv.max()), "accel": bool(fixed),
-                   "max_iter": args.max_iter,
+                   "max_iter": max_iter,
                    "final_gap_median": float(np.median(r["gap"].cpu().numpy())),
                    "final_gap_max": float(np.nanmax(r["gap"].cpu().numpy())),
                    "tables": "one float64 table on [0, t_max] for every point and candidate" if fixed else
@@ -961,7 +964,7 @@ def main():
                     help="chain_ttr workload: fixed-step rule with one shared table, or Eq. 17 per point")
     ap.add_argument("--train-points", type=int, default=8192, help="chain warm start: labelled training points")
     ap.add_argument("--train-epochs", type=int, default=60, help="chain warm start: training epochs")
-    ap.add_argument("--max-iter", type=int, default=400000,
+    ap.add_argument("--max-iter", type=int, default=MAX_ITER_DEFAULT,
                     help="secondary workloads: iteration cap (small values only for profiler captures)")
     args = ap.parse_args()
     if args.workload == "trajectory" and args.impl == "ours":
