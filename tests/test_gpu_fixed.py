@@ -173,6 +173,30 @@ def test_fixed_step_time_to_reach_fp64_double_integrator(H, newton):
     assert np.all(np.abs(T - ref["T"]) <= 1e-6 * np.maximum(ref["T"], 1e-3)), (T, ref["T"])
 
 
+def test_fixed_step_time_to_reach_warm_bracket_and_start(H):
+    # a bracket around T* and a warm p_init (the oracle's p* at T*) give the
+    # same T*; a bracket below T* is detected and replaced by [0, t_max]
+    import torch
+    from oracle import hopf as oh
+    sysd = wl.double_integrator(0.1)
+    w = wl.workload_di(8)
+    ref = oh.time_to_reach(sysd, w["x"], 8.0, 512, oh.FixedStep(8.0, 512), tau=2.0, tol_T=1e-9, tol_gap=1e-10,
+                           variables="terminal")
+    opts = H.Options(rule=H.LEFT_FIXED, N=512, t_max=8.0, tau=2.0, tol_gap=1e-10, tol_T=1e-8, precision=H.FP64,
+                     max_iter=2000000, variables=TERM)
+    S = H.System.from_dict(sysd)
+    x = cuda(w["x"], torch.float64)
+    lo = cuda(ref["T"] * 0.9, torch.float64)
+    hi = cuda(np.minimum(ref["T"] * 1.1, 8.0), torch.float64)
+    r = H.time_to_reach(S, x, opts, T_lo=lo, T_hi=hi, p_init=cuda(ref["p"], torch.float64))
+    assert np.all(np.isin(r["status"].cpu().numpy(), (0, 4)))
+    assert np.all(np.abs(np_(r["T"]) - ref["T"]) <= 1e-6 * ref["T"]), (np_(r["T"]), ref["T"])
+    lo2 = cuda(ref["T"] * 0.5, torch.float64)
+    hi2 = cuda(ref["T"] * 0.8, torch.float64)
+    r2 = H.time_to_reach(S, x, opts, T_lo=lo2, T_hi=hi2)
+    assert np.all(np.abs(np_(r2["T"]) - ref["T"]) <= 1e-6 * ref["T"]), (np_(r2["T"]), ref["T"])
+
+
 @pytest.mark.parametrize("newton", [False, True])
 def test_fixed_step_time_to_reach_fp32_chain_tile(H, newton):
     # tiled kernel in sign mode (n = 20): 24 points, three against the oracle
