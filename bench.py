@@ -846,7 +846,7 @@ def run_c4(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; 100-mass chain, x~N(0,I))",
         "config": {"workload": f"c4_warm_start_spring_chain_n200_m10_box_N512_T10_value_{points}pts",
                    "n": n, "m": m, "N": N, "t": T, "points_per_gpu": points, "tol_gap": TOL, "tau": C4["tau"],
-                   "solve": "value at a shared horizon (time-to-reach at this size: see DESIGN)",
+                   "solve": "value at a shared horizon (a time-to-reach search per point at this size needs ~20 rounds of 1e4-iteration solves)",
                    "start": "warm (network prediction of p*), cold fallback",
                    "iteration": "Eq. 15 in terminal-time variables p = e^{TA^T} q, tensor-core kernel (3 x tf32)",
                    "l2": "flushed between timed steps (512 MB write)",
